@@ -1,0 +1,83 @@
+"""Seeded synthetic inputs for the AIFMM workloads.
+
+This module is shared by the FP64 oracle and by the CUDA path.  It draws
+random numbers and names workloads; it holds none of the method's
+arithmetic (no tree, no kernel evaluation, no factorisation).
+
+Recipe (the paper's experiments all use synthetic inputs, Sec. 4): the
+points are i.i.d. uniform in a box, drawn with numpy's PCG64
+``default_rng(seed)`` as one ``uniform(lo, hi, (N, d))`` call; the
+right-hand sides are drawn afterwards from the same generator as
+``standard_normal((nrhs, N))`` and transposed, so that column k of an
+nrhs-column draw is the k-th block of N normals (the nrhs=1 draw is the
+first column of the nrhs=64 draw).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# kernel kinds, in the order of the C-ABI enum
+LOG2D, INVR3D, INVR2D, GAUSS = 0, 1, 2, 3
+KERNEL_NAMES = {LOG2D: "log2d", INVR3D: "invr3d", INVR2D: "invr2d", GAUSS: "gauss"}
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    dim: int
+    lo: float
+    hi: float
+    seed: int
+    kernel: int
+    diag: float            # value of A_ii
+    leaf: int              # n_max, target points per leaf box
+    tol: float             # NNCA / RRQR tolerance eps_A
+    nrhs: int = 1
+    length: float = 1.0    # Gaussian length scale
+    extra: dict = field(default_factory=dict)
+
+
+def points_and_rhs(w: Workload, nrhs: int | None = None):
+    """Return (points (N, d) float64, rhs (N, nrhs) float64) for workload w."""
+    k = w.nrhs if nrhs is None else nrhs
+    rng = np.random.default_rng(w.seed)
+    pts = rng.uniform(w.lo, w.hi, (w.n, w.dim))
+    b = rng.standard_normal((k, w.n)).T.copy()
+    return np.ascontiguousarray(pts), np.asfortranarray(b)
+
+
+def log2d(n: int, seed: int, leaf: int = 64, tol: float = 1e-10, nrhs: int = 1,
+          diag: float | None = None) -> Workload:
+    """2D log kernel A_ij = log|x_i - x_j|, A_ii = N (the diagonal of the
+    spec 2D configurations), points uniform in [-1,1]^2."""
+    return Workload(f"log2d_N{n}", n, 2, -1.0, 1.0, seed, LOG2D,
+                    float(n) if diag is None else diag, leaf, tol, nrhs)
+
+
+def invr2d(n: int, seed: int, leaf: int = 64, tol: float = 1e-10, nrhs: int = 1) -> Workload:
+    """2D 1/r kernel with A_ii = sqrt(1000 N) (Sec. 4.3, Experiment 3)."""
+    return Workload(f"invr2d_N{n}", n, 2, -1.0, 1.0, seed, INVR2D,
+                    math.sqrt(1000.0 * n), leaf, tol, nrhs)
+
+
+def invr3d(n: int, seed: int, leaf: int = 64, tol: float = 1e-6, nrhs: int = 1) -> Workload:
+    """3D 1/r kernel with A_ii = N^(2/3), points uniform in [-1,1]^3."""
+    return Workload(f"invr3d_N{n}", n, 3, -1.0, 1.0, seed, INVR3D,
+                    float(n) ** (2.0 / 3.0), leaf, tol, nrhs)
+
+
+def gauss2d(n: int, seed: int, leaf: int = 64, tol: float = 1e-10, nrhs: int = 1) -> Workload:
+    """GP-style kernel exp(-|x-y|^2/0.1^2) + 1e-2 I on [0,1]^2."""
+    return Workload(f"gauss2d_N{n}", n, 2, 0.0, 1.0, seed, GAUSS, 1.0 + 1e-2,
+                    leaf, tol, nrhs, length=0.1)
+
+
+# The named configurations: the small case the oracle finishes in seconds and
+# the single-GPU benchmark case (same kernel and dimension, nrhs 1 and 64).
+SMALL = log2d(4096, seed=0)
+BENCH = log2d(65536, seed=1)
+BENCH64 = log2d(65536, seed=1, nrhs=64)
