@@ -1,0 +1,156 @@
+/*
+ * aifmm.h -- C ABI of the GB300 (sm_103a) AIFMM factorisation and solve.
+ *
+ * The library solves A x = b for a dense N-body interaction matrix A
+ * (A_ij = kernel(u_i, v_j), sources = targets) with the Algebraic Inverse
+ * Fast Multipole Method of Gujjula & Ambikasaran (arXiv 2301.12704):
+ *   build  -- uniform 2^d tree and interaction lists (Sec. 2.1-2.2), NNCA
+ *             operators (Sec. 2.3), extended sparse system (Sec. 3.1);
+ *   factor -- level-by-level elimination with fill-ins updated first and
+ *             compressed/redirected once (Algorithm 2, Sec. 3.2-3.5);
+ *   solve  -- right-hand-side Schur operations, top solve, back
+ *             substitution (Algorithm 3, Sec. 3.6).
+ * Every numerical step runs in CUDA kernels on the current device; the host
+ * only sequences launches and reads back a few rank counts per level.
+ *
+ * Conventions for every entry point
+ *   Pointers: a "buffer" argument may point to host or device memory; the
+ *     library detects which (cudaPointerGetAttributes) and copies host data
+ *     through pinned staging on the handle's stream.  Device buffers must be
+ *     on the handle's device.
+ *   Layout: points are row-major N x dim (point-major); right-hand sides and
+ *     solutions are column-major N x nrhs with leading dimension ld >= N, in
+ *     the caller's original point order.
+ *   Ownership: build copies the points; the caller keeps ownership of every
+ *     buffer it passes.  The handle owns all device memory it allocates until
+ *     aifmm_destroy.
+ *   Errors: every call returns an aifmm_status; nothing aborts, traps or
+ *     throws across the ABI.  aifmm_last_error(h) gives a message.  Device
+ *     kernels report errors through a status word that the host reads after
+ *     the call's work completes (calls are synchronous on return).
+ *   Threads: one handle is used by one host thread at a time.
+ */
+#ifndef AIFMM_H
+#define AIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aifmm_ctx* aifmm_h;
+
+typedef enum {
+  AIFMM_OK = 0,
+  AIFMM_ERR_INVALID = 1,   /* bad argument: n < 1, dim not 2/3, tol < 0, leaf < 1,
+                              duplicate points, null pointer, nrhs < 1, ld < n */
+  AIFMM_ERR_OOM = 2,       /* device allocation failed */
+  AIFMM_ERR_SINGULAR = 3,  /* a pivot block was numerically singular */
+  AIFMM_ERR_STATE = 4,     /* e.g. solve before factor */
+  AIFMM_ERR_NOCONV = 5,    /* iterative solve did not converge */
+  AIFMM_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+  AIFMM_ERR_TIMEOUT = 7,   /* a bounded device wait ran out */
+  AIFMM_ERR_CAPACITY = 8   /* a size exceeded a compiled-in capacity */
+} aifmm_status;
+
+/* Kernels (Sec. 4): off-diagonal entries as a function of r = |x_i - x_j|.
+ *   LOG2D  log r               (Experiment 4 kernel), dim 2
+ *   INVR3D 1/r                 dim 3
+ *   INVR2D 1/r                 (Experiment 3 kernel), dim 2
+ *   GAUSS  exp(-r^2/length^2)  dim 2 or 3
+ * The diagonal A_ii is `diag`. */
+typedef enum { AIFMM_K_LOG2D = 0, AIFMM_K_INVR3D = 1, AIFMM_K_INVR2D = 2, AIFMM_K_GAUSS = 3 } aifmm_kernel_kind;
+
+typedef struct {
+  int kind;        /* aifmm_kernel_kind */
+  int dim;         /* 2 or 3 */
+  double diag;     /* A_ii */
+  double length;   /* Gaussian length scale (GAUSS only) */
+} aifmm_kernel;
+
+typedef struct {
+  int order;       /* 0: distance-2 colour order (default), only value supported */
+  int depth;       /* 0: depth from the average-occupancy rule; >= 2: force depth L */
+  void* stream;    /* cudaStream_t to run on; NULL = the library's own stream */
+} aifmm_options;
+
+/* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of
+ * the last call of each kind. */
+typedef struct {
+  int64_t n;
+  int dim;
+  int levels;               /* L */
+  int max_rank_nnca;        /* max NNCA rank over levels 2..L */
+  int max_rank_factor;      /* r_m: max rank after compress and redirect */
+  int max_m;                /* largest pivot x-size over all levels */
+  int top_size;             /* size of the dense level-1 system */
+  double flops_factor;      /* algorithmic FP64 flops of the last factor */
+  double bytes_solve;       /* algorithmic bytes streamed by one solve sweep pair, nrhs=1 */
+  double bytes_resident;    /* device bytes held by the handle */
+  double ms_build, ms_factor, ms_solve, ms_matvec;
+} aifmm_stats_t;
+
+/* Build the tree, interaction lists, NNCA operators and extended system.
+ *   points    N x dim row-major (host or device), copied.
+ *   n         number of points N >= 1.
+ *   k         kernel description (dim must be 2 or 3).
+ *   tol       eps_A >= 0, shared by NNCA and RRQR (Sec. 4, notation table).
+ *   leaf_size n_max >= 1, target points per leaf box (Algorithm 2, first step).
+ *   opt       may be NULL (defaults).
+ *   out       receives the new handle (NULL on failure).
+ * Errors: INVALID, OOM, CUDA, CAPACITY. */
+aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k, double tol,
+                         int leaf_size, const aifmm_options* opt, aifmm_h* out);
+
+/* Algorithm 2: eliminate levels L..2 (distance-2 colour batches), compress
+ * and redirect pending well-separated fill-ins once per box, factor the top
+ * dense level-1 system.  Independent of any right-hand side (Remark, Sec. 3.6).
+ * Errors: STATE (no build), SINGULAR, OOM, CUDA, CAPACITY. */
+aifmm_status aifmm_factor(aifmm_h h);
+
+/* Algorithm 3: x = A^-1 rhs through the factorisation.
+ *   rhs, x    N x nrhs column-major, leading dimension ld (host or device;
+ *             may alias).  Original point order.
+ * Errors: STATE (no factor), INVALID, OOM, CUDA. */
+aifmm_status aifmm_solve(aifmm_h h, const double* rhs, double* x, int nrhs, int64_t ld);
+
+/* y = A_H2 x with the NNCA H^2 representation built by aifmm_build
+ * (upward P2M/M2M, M2L, downward L2L/L2P, near-field P2P).
+ * Errors: STATE, INVALID, OOM, CUDA. */
+aifmm_status aifmm_matvec(aifmm_h h, const double* x, double* y, int nrhs, int64_t ld);
+
+/* y = A x with every entry of A evaluated (exact O(N^2) direct sum on the
+ * GPU); used to measure true residuals. Errors: STATE, INVALID, OOM, CUDA. */
+aifmm_status aifmm_direct_matvec(aifmm_h h, const double* x, double* y, int nrhs, int64_t ld);
+
+/* Statistics of the handle. */
+aifmm_status aifmm_stats(aifmm_h h, aifmm_stats_t* out);
+
+/* Introspection for parity checks (host buffers only).
+ *   aifmm_tree_perm: perm[k] = original index of the k-th point in tree order
+ *     (N entries); level_start (may be NULL) receives the leaf-box starts
+ *     (2^(dim*L) + 1 entries).
+ *   aifmm_level_ranks: for level l in [2, L], NNCA ranks (which = 0) or
+ *     ranks after factorisation (which = 1) of the 2^(dim*l) boxes.
+ *   aifmm_level_pivots: for level l, the incoming row pivots t^{b,i} of
+ *     every box as tree positions, concatenated in box order (sum of NNCA
+ *     ranks entries). */
+aifmm_status aifmm_tree_perm(aifmm_h h, int64_t* perm, int64_t* level_start);
+aifmm_status aifmm_level_ranks(aifmm_h h, int level, int which, int* ranks);
+aifmm_status aifmm_level_pivots(aifmm_h h, int level, int64_t* pivots);
+
+/* Depth L of the handle's tree (0 if h is NULL). */
+int aifmm_levels(aifmm_h h);
+
+/* Message of the last error on h (or of the last failed aifmm_build when h is
+ * NULL).  Valid until the next call on the handle. */
+const char* aifmm_last_error(aifmm_h h);
+
+/* Free every device and host resource of h. NULL is a no-op. */
+void aifmm_destroy(aifmm_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIFMM_H */

@@ -1,0 +1,207 @@
+"""Python binding of the GB300 AIFMM library (include/aifmm.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library
+``libaifmm.so`` built in-tree for sm_103a (``_build.build()``).  Importing
+this module does not load the library; the first call does, and raises if
+the library is missing or no CUDA device is present -- there is no CPU path.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or device);
+float64, C-contiguous points (N x dim) and Fortran-ordered / column-major
+right-hand sides (N x nrhs).  Names follow the C ABI: aifmm_build,
+aifmm_factor, aifmm_solve, aifmm_matvec, aifmm_direct_matvec, aifmm_stats,
+aifmm_tree_perm, aifmm_level_ranks, aifmm_level_pivots, aifmm_destroy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaifmm.so")
+HEADER = os.path.join(HERE, "..", "include", "aifmm.h")
+
+LOG2D, INVR3D, INVR2D, GAUSS = 0, 1, 2, 3
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_SINGULAR", 4: "ERR_STATE",
+          5: "ERR_NOCONV", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
+
+
+class AifmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dim", C.c_int), ("diag", C.c_double), ("length", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dim", C.c_int), ("levels", C.c_int), ("max_rank_nnca", C.c_int),
+                ("max_rank_factor", C.c_int), ("max_m", C.c_int), ("top_size", C.c_int),
+                ("flops_factor", C.c_double), ("bytes_solve", C.c_double), ("bytes_resident", C.c_double),
+                ("ms_build", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("ms_matvec", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libaifmm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, dbl, cint = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        L.aifmm_build.argtypes = [vp, i64, C.POINTER(Kernel), dbl, cint, C.POINTER(Options), C.POINTER(vp)]
+        L.aifmm_factor.argtypes = [vp]
+        L.aifmm_solve.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_matvec.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_direct_matvec.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.aifmm_tree_perm.argtypes = [vp, vp, vp]
+        L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
+        L.aifmm_level_pivots.argtypes = [vp, cint, vp]
+        L.aifmm_levels.argtypes = [vp]
+        L.aifmm_last_error.argtypes = [vp]
+        L.aifmm_last_error.restype = C.c_char_p
+        L.aifmm_destroy.argtypes = [vp]
+        L.aifmm_destroy.restype = None
+        for name in ("aifmm_build", "aifmm_factor", "aifmm_solve", "aifmm_matvec", "aifmm_direct_matvec",
+                     "aifmm_stats", "aifmm_tree_perm", "aifmm_level_ranks", "aifmm_level_pivots",
+                     "aifmm_levels"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().aifmm_last_error(handle)
+        raise AifmmError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, a
+    return a.data_ptr(), a
+
+
+class Handle:
+    """Owns one aifmm_h."""
+
+    def __init__(self, raw, n, dim):
+        self.raw, self.n, self.dim = raw, n, dim
+
+    def __del__(self):
+        try:
+            aifmm_destroy(self)
+        except Exception:
+            pass
+
+
+def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
+                depth: int = 0, stream=None) -> Handle:
+    """Build tree, lists, NNCA operators and the extended system (C: aifmm_build)."""
+    if isinstance(points, np.ndarray):
+        points = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = points.shape
+    k = Kernel(kernel, dim, float(diag), float(length))
+    o = Options(0, int(depth), C.c_void_p(stream) if stream else None)
+    out = C.c_void_p()
+    p, keep = _ptr(points)
+    _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
+    return Handle(out.value, n, dim)
+
+
+def aifmm_factor(h: Handle) -> None:
+    _check(lib().aifmm_factor(h.raw), h.raw)
+
+
+def _col_major(a):
+    """Column-major float64 copy/view of a vector or N x nrhs matrix."""
+    if isinstance(a, np.ndarray):
+        return np.asfortranarray(a[:, None] if a.ndim == 1 else a, dtype=np.float64)
+    t = a[:, None] if a.dim() == 1 else a
+    return t.t().contiguous().t()
+
+
+def _empty_cm(a):
+    if isinstance(a, np.ndarray):
+        return np.empty(a.shape, dtype=np.float64, order="F")
+    import torch
+    return torch.empty((a.shape[1], a.shape[0]), dtype=a.dtype, device=a.device).t()
+
+
+def aifmm_solve(h: Handle, rhs):
+    """x = A^-1 rhs (C: aifmm_solve); rhs N or N x nrhs, original order."""
+    b = _col_major(rhs)
+    x = _empty_cm(b)
+    pb, kb = _ptr(b)
+    px, kx = _ptr(x)
+    _check(lib().aifmm_solve(h.raw, C.c_void_p(pb), C.c_void_p(px), b.shape[1], h.n), h.raw)
+    return x
+
+
+def _product(fn, h, xv):
+    xx = _col_major(xv)
+    y = _empty_cm(xx)
+    px, kx = _ptr(xx)
+    py, ky = _ptr(y)
+    _check(fn(h.raw, C.c_void_p(px), C.c_void_p(py), xx.shape[1], h.n), h.raw)
+    return y
+
+
+def aifmm_matvec(h: Handle, x):
+    """y = A_H2 x with the NNCA operators (C: aifmm_matvec)."""
+    return _product(lib().aifmm_matvec, h, x)
+
+
+def aifmm_direct_matvec(h: Handle, x):
+    """y = A x, every entry evaluated (C: aifmm_direct_matvec)."""
+    return _product(lib().aifmm_direct_matvec, h, x)
+
+
+def aifmm_stats(h: Handle) -> dict:
+    s = Stats()
+    _check(lib().aifmm_stats(h.raw, C.byref(s)), h.raw)
+    return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def aifmm_levels(h: Handle) -> int:
+    return lib().aifmm_levels(h.raw)
+
+
+def aifmm_tree_perm(h: Handle):
+    L = aifmm_levels(h)
+    perm = np.empty(h.n, dtype=np.int64)
+    starts = np.empty((1 << (h.dim * L)) + 1, dtype=np.int64)
+    _check(lib().aifmm_tree_perm(h.raw, C.c_void_p(perm.ctypes.data), C.c_void_p(starts.ctypes.data)), h.raw)
+    return perm, starts
+
+
+def aifmm_level_ranks(h: Handle, level: int, which: int = 0):
+    r = np.empty(1 << (h.dim * level), dtype=np.int32)
+    _check(lib().aifmm_level_ranks(h.raw, level, which, C.c_void_p(r.ctypes.data)), h.raw)
+    return r
+
+
+def aifmm_level_pivots(h: Handle, level: int):
+    r = aifmm_level_ranks(h, level, 0)
+    p = np.empty(int(r.sum()), dtype=np.int64)
+    _check(lib().aifmm_level_pivots(h.raw, level, C.c_void_p(p.ctypes.data)), h.raw)
+    return p
+
+
+def aifmm_destroy(h: Handle) -> None:
+    if h is not None and h.raw:
+        lib().aifmm_destroy(h.raw)
+        h.raw = None

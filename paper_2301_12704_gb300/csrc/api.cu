@@ -1,0 +1,412 @@
+// C ABI of the library (include/aifmm.h): argument checks, device memory of
+// the handle, host/device pointer handling, timing, and the calls into the
+// tree, NNCA, factorisation and solve launchers.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "../../include/aifmm.h"
+#include "internal.h"
+
+using namespace aifmm;
+
+struct aifmm_ctx {
+  Handle h;
+};
+
+static std::string g_build_err;
+
+namespace aifmm {
+
+// optional fault injection for tests of the out-of-memory path: the k-th
+// device allocation of a handle fails when AIFMM_FAIL_ALLOC_AT=k is set.
+static long fail_at() {
+  const char* s = std::getenv("AIFMM_FAIL_ALLOC_AT");
+  return s ? std::atol(s) : 0;
+}
+
+void* halloc(Handle& h, size_t bytes, bool zero) {
+  static thread_local long counter = 0;
+  long f = fail_at();
+  if (f > 0 && ++counter == f) {
+    h.err = "device allocation failed (injected)";
+    return nullptr;
+  }
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h.err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+    return nullptr;
+  }
+  if (zero && cudaMemsetAsync(p, 0, bytes, h.stream) != cudaSuccess) {
+    cudaFree(p);
+    h.err = "cudaMemsetAsync failed";
+    return nullptr;
+  }
+  h.allocs.push_back(p);
+  h.resident += bytes;
+  return p;
+}
+
+void* hscratch(Handle& h, int slot, size_t bytes) {
+  if ((int)h.scratch.size() <= slot) h.scratch.resize(slot + 1, {nullptr, 0});
+  auto& s = h.scratch[slot];
+  if (s.second >= bytes && s.first) return s.first;
+  if (s.first) {
+    cudaStreamSynchronize(h.stream);
+    cudaFree(s.first);
+    h.resident -= s.second;
+    s.first = nullptr;
+    s.second = 0;
+  }
+  void* p = nullptr;
+  size_t b = bytes < 16 ? 16 : bytes;
+  if (cudaMalloc(&p, b) != cudaSuccess) {
+    cudaGetLastError();
+    h.err = "cudaMalloc of scratch (" + std::to_string(b) + " bytes) failed";
+    return nullptr;
+  }
+  s.first = p;
+  s.second = b;
+  h.resident += b;
+  return p;
+}
+
+void hfree_all(Handle& h) {
+  if (h.stream) cudaStreamSynchronize(h.stream);
+  for (void* p : h.allocs) cudaFree(p);
+  h.allocs.clear();
+  for (auto& s : h.scratch)
+    if (s.first) cudaFree(s.first);
+  h.scratch.clear();
+  h.resident = 0;
+}
+
+int check_derr(Handle& h) {
+  int v = 0;
+  cudaMemcpy(&v, h.derr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (v) cudaMemset(h.derr, 0, sizeof(int));
+  return v;
+}
+
+}  // namespace aifmm
+
+static aifmm_status to_status(int e) {
+  switch (e) {
+    case HOK: return AIFMM_OK;
+    case HINVALID: return AIFMM_ERR_INVALID;
+    case HOOM: return AIFMM_ERR_OOM;
+    case HSINGULAR: return AIFMM_ERR_SINGULAR;
+    case HSTATE: return AIFMM_ERR_STATE;
+    case HCAPACITY: return AIFMM_ERR_CAPACITY;
+    default: return AIFMM_ERR_CUDA;
+  }
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+  }
+};
+
+extern "C" {
+
+aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k, double tol, int leaf_size,
+                         const aifmm_options* opt, aifmm_h* out) {
+  if (out) *out = nullptr;
+  g_build_err.clear();
+  if (!points || !k || !out || n < 1 || n > (int64_t)1 << 30 || (k->dim != 2 && k->dim != 3) ||
+      !(tol >= 0.0) || leaf_size < 1 || k->kind < 0 || k->kind > 3 || !std::isfinite(k->diag) ||
+      (k->kind == AIFMM_K_GAUSS && !(k->length > 0.0)) || (opt && opt->order != 0) ||
+      (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12))) {
+    g_build_err = "invalid argument";
+    return AIFMM_ERR_INVALID;
+  }
+  aifmm_ctx* c = new aifmm_ctx();
+  Handle& h = c->h;
+  cudaGetDevice(&h.device);
+  h.N = n;
+  h.d = k->dim;
+  h.tol = tol;
+  h.leaf = leaf_size;
+  h.kp.kind = k->kind;
+  h.kp.dim = k->dim;
+  h.kp.diag = k->diag;
+  h.kp.inv_len2 = k->kind == AIFMM_K_GAUSS ? 1.0 / (k->length * k->length) : 0.0;
+  if (opt && opt->stream) {
+    h.stream = (cudaStream_t)opt->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      g_build_err = "cudaStreamCreate failed";
+      delete c;
+      return AIFMM_ERR_CUDA;
+    }
+    h.own_stream = true;
+  }
+  // depth: average-occupancy rule L = max(2, min l with (2^d)^l * n_max >= N)
+  int L = 2;
+  while (((int64_t)1 << (h.d * L)) * leaf_size < n) ++L;
+  if (opt && opt->depth) L = opt->depth;
+  h.L = L;
+  if (h.d * L > 30) {
+    g_build_err = "tree too deep";
+    aifmm_destroy(c);
+    return AIFMM_ERR_CAPACITY;
+  }
+  Timer tm(h.stream);
+  int e = HOK;
+  h.derr = hnew<int>(h, 1);
+  if (!h.derr) e = HOOM;
+  const double* pdev = points;
+  if (!e && !is_device_ptr(points)) {
+    double* tmp = hnew<double>(h, (size_t)n * h.d, false);
+    if (!tmp) e = HOOM;
+    else if (cudaMemcpyAsync(tmp, points, sizeof(double) * n * h.d, cudaMemcpyHostToDevice, h.stream) != cudaSuccess)
+      e = HCUDA;
+    pdev = tmp;
+  }
+  if (!e) e = build_tree(h, pdev);
+  if (!e) e = build_nnca(h);
+  if (!e) {
+    cudaError_t ce = cudaStreamSynchronize(h.stream);
+    if (ce != cudaSuccess) {
+      h.err = cudaGetErrorString(ce);
+      e = HCUDA;
+    }
+  }
+  h.ms_build = tm.stop();
+  if (e) {
+    g_build_err = h.err.empty() ? "build failed" : h.err;
+    aifmm_destroy(c);
+    return to_status(e);
+  }
+  h.built = true;
+  *out = c;
+  return AIFMM_OK;
+}
+
+aifmm_status aifmm_factor(aifmm_h c) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (!h.built) {
+    h.err = "factor before build";
+    return AIFMM_ERR_STATE;
+  }
+  if (h.factored) {
+    // refactor from scratch: drop the previous factor storage
+    h.err = "handle already factored";
+    return AIFMM_ERR_STATE;
+  }
+  Timer tm(h.stream);
+  int e = run_factor(h);
+  if (!e) {
+    cudaError_t ce = cudaStreamSynchronize(h.stream);
+    if (ce != cudaSuccess) {
+      h.err = cudaGetErrorString(ce);
+      e = HCUDA;
+    }
+  }
+  h.ms_factor = tm.stop();
+  if (e) return to_status(e);
+  h.factored = true;
+  return AIFMM_OK;
+}
+
+// copy a column-major N x nrhs (ld) operand into the device buffer dst (ld)
+static int stage_in(Handle& h, const double* src, double* dst, int nrhs, int64_t ld) {
+  cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (src == dst) return HOK;
+  AIFMM_CUDA_TRY(h, cudaMemcpy2DAsync(dst, ld * sizeof(double), src, ld * sizeof(double), h.N * sizeof(double),
+                                      nrhs, kind, h.stream));
+  return HOK;
+}
+
+aifmm_status aifmm_solve(aifmm_h c, const double* rhs, double* x, int nrhs, int64_t ld) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (!h.factored) {
+    h.err = "solve before factor";
+    return AIFMM_ERR_STATE;
+  }
+  if (!rhs || !x || nrhs < 1 || ld < h.N) {
+    h.err = "invalid argument";
+    return AIFMM_ERR_INVALID;
+  }
+  Timer tm(h.stream);
+  bool xdev = is_device_ptr(x);
+  double* work = xdev ? x : (double*)hscratch(h, 90, sizeof(double) * ld * nrhs);
+  if (!work) return AIFMM_ERR_OOM;
+  int e = stage_in(h, rhs, work, nrhs, ld);
+  if (!e) e = run_solve(h, work, nrhs, ld);
+  if (!e && !xdev) {
+    if (cudaMemcpy2DAsync(x, ld * sizeof(double), work, ld * sizeof(double), h.N * sizeof(double), nrhs,
+                          cudaMemcpyDeviceToHost, h.stream) != cudaSuccess)
+      e = HCUDA;
+  }
+  if (!e && cudaStreamSynchronize(h.stream) != cudaSuccess) {
+    h.err = "solve: CUDA error";
+    e = HCUDA;
+  }
+  h.ms_solve = tm.stop();
+  if (!e) {
+    int de = check_derr(h);
+    if (de) {
+      h.err = "solve: device error " + std::to_string(de);
+      e = HCAPACITY;
+    }
+  }
+  return to_status(e);
+}
+
+static aifmm_status product(aifmm_h c, const double* x, double* y, int nrhs, int64_t ld, bool direct) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (!h.built) {
+    h.err = "matvec before build";
+    return AIFMM_ERR_STATE;
+  }
+  if (!x || !y || nrhs < 1 || ld < h.N) {
+    h.err = "invalid argument";
+    return AIFMM_ERR_INVALID;
+  }
+  Timer tm(h.stream);
+  bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+  const double* xin = x;
+  int e = HOK;
+  if (!xdev) {
+    double* t = (double*)hscratch(h, 91, sizeof(double) * ld * nrhs);
+    if (!t) return AIFMM_ERR_OOM;
+    e = stage_in(h, x, t, nrhs, ld);
+    xin = t;
+  }
+  double* yout = ydev ? y : (double*)hscratch(h, 92, sizeof(double) * ld * nrhs);
+  if (!yout) return AIFMM_ERR_OOM;
+  if (!e) e = direct ? run_direct_matvec(h, xin, yout, nrhs, ld) : run_h2_matvec(h, xin, yout, nrhs, ld);
+  if (!e && !ydev) {
+    if (cudaMemcpy2DAsync(y, ld * sizeof(double), yout, ld * sizeof(double), h.N * sizeof(double), nrhs,
+                          cudaMemcpyDeviceToHost, h.stream) != cudaSuccess)
+      e = HCUDA;
+  }
+  if (!e && cudaStreamSynchronize(h.stream) != cudaSuccess) e = HCUDA;
+  h.ms_matvec = tm.stop();
+  return to_status(e);
+}
+
+aifmm_status aifmm_matvec(aifmm_h c, const double* x, double* y, int nrhs, int64_t ld) {
+  return product(c, x, y, nrhs, ld, false);
+}
+
+aifmm_status aifmm_direct_matvec(aifmm_h c, const double* x, double* y, int nrhs, int64_t ld) {
+  return product(c, x, y, nrhs, ld, true);
+}
+
+aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {
+  if (!c || !o) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  std::memset(o, 0, sizeof(*o));
+  o->n = h.N;
+  o->dim = h.d;
+  o->levels = h.L;
+  o->max_rank_nnca = h.max_rank_nnca;
+  o->max_rank_factor = h.max_rank_factor;
+  o->max_m = h.max_m;
+  o->top_size = h.ntop;
+  o->flops_factor = h.flops_factor;
+  double bytes = 0;
+  for (auto& F : h.fac) {
+    if (!F.nb) continue;
+    for (int b = 0; b < F.nb; ++b) {
+      double m = F.h_m[b], r = F.h_r[b], n = m + r;
+      // pivot LU + the coupled panels, read once per sweep (upper bound: 3^d blocks)
+      bytes += 8.0 * (n * n + 2.0 * std::pow(3.0, h.d) * m * m);
+    }
+  }
+  o->bytes_solve = bytes;
+  o->bytes_resident = (double)h.resident;
+  o->ms_build = h.ms_build;
+  o->ms_factor = h.ms_factor;
+  o->ms_solve = h.ms_solve;
+  o->ms_matvec = h.ms_matvec;
+  return AIFMM_OK;
+}
+
+aifmm_status aifmm_tree_perm(aifmm_h c, int64_t* perm, int64_t* level_start) {
+  if (!c || !perm) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  std::vector<int> p(h.N);
+  if (cudaMemcpy(p.data(), h.perm, sizeof(int) * h.N, cudaMemcpyDeviceToHost) != cudaSuccess) return AIFMM_ERR_CUDA;
+  for (int64_t i = 0; i < h.N; ++i) perm[i] = p[i];
+  if (level_start)
+    for (size_t i = 0; i < h.h_leaf_start.size(); ++i) level_start[i] = h.h_leaf_start[i];
+  return AIFMM_OK;
+}
+
+aifmm_status aifmm_level_ranks(aifmm_h c, int level, int which, int* ranks) {
+  if (!c || !ranks) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (level < 2 || level > h.L) return AIFMM_ERR_INVALID;
+  if (which == 0) {
+    const auto& v = h.nn[level].h_rank;
+    std::memcpy(ranks, v.data(), sizeof(int) * v.size());
+    return AIFMM_OK;
+  }
+  if (!h.factored) return AIFMM_ERR_STATE;
+  const auto& v = h.fac[level].h_r;
+  std::memcpy(ranks, v.data(), sizeof(int) * v.size());
+  return AIFMM_OK;
+}
+
+aifmm_status aifmm_level_pivots(aifmm_h c, int level, int64_t* pivots) {
+  if (!c || !pivots) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (level < 2 || level > h.L) return AIFMM_ERR_INVALID;
+  const NnLevel& N = h.nn[level];
+  std::vector<int> p((size_t)N.nb * N.R);
+  if (cudaMemcpy(p.data(), N.pivpos, sizeof(int) * p.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return AIFMM_ERR_CUDA;
+  size_t o = 0;
+  for (int b = 0; b < N.nb; ++b)
+    for (int k = 0; k < N.h_rank[b]; ++k) pivots[o++] = p[(size_t)b * N.R + k];
+  return AIFMM_OK;
+}
+
+int aifmm_levels(aifmm_h c) { return c ? c->h.L : 0; }
+
+const char* aifmm_last_error(aifmm_h c) {
+  if (!c) return g_build_err.c_str();
+  return c->h.err.c_str();
+}
+
+void aifmm_destroy(aifmm_h c) {
+  if (!c) return;
+  Handle& h = c->h;
+  hfree_all(h);
+  if (h.own_stream && h.stream) cudaStreamDestroy(h.stream);
+  delete c;
+}
+
+}  // extern "C"

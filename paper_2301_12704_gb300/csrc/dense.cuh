@@ -1,0 +1,203 @@
+// Batched dense FP64 building blocks used by the factorisation, the top
+// solve and the sweeps: blocked right-looking LU with partial pivoting
+// (panel / TRSM / trailing GEMM launches), multi-RHS LU solve, and a 64x64
+// register-tiled GEMM tile.
+#pragma once
+#include "common.cuh"
+
+namespace aifmm {
+
+struct LuItem {
+  double* a;       // column-major n x n, leading dimension ld
+  int* ipiv;       // n row interchanges (LAPACK convention, 0-based)
+  const double* colmax;  // n column maxima of the original matrix (singularity test)
+  int n, ld;
+};
+
+constexpr int LU_NB = 32;
+
+// panel k0..k0+NB-1: pivot search, full-row interchange, scaling, rank-1
+// updates inside the panel.  One block per item.
+static __global__ void __launch_bounds__(256) k_lu_panel(const LuItem* items, int k0, int* err) {
+  __shared__ double shv[32];
+  __shared__ int shi[32];
+  LuItem it = items[blockIdx.x];
+  int n = it.n;
+  if (k0 >= n) return;
+  double* A = it.a;
+  const int ld = it.ld;
+  int kend = min(n, k0 + LU_NB);
+  for (int j = k0; j < kend; ++j) {
+    ArgMax best;
+    best.v = -1.0;
+    best.i = -1;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      ArgMax c;
+      c.v = fabs(A[i + (size_t)j * ld]);
+      c.i = i;
+      best = amax_pick(best, c);
+    }
+    best = block_amax(best, shv, shi);
+    int p = best.i;
+    double cm = it.colmax ? it.colmax[j] : 0.0;
+    if (!(best.v > 1e-14 * cm) || !(best.v > 0.0)) {
+      if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
+      return;
+    }
+    if (threadIdx.x == 0) it.ipiv[j] = p;
+    if (p != j)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double t = A[j + (size_t)c * ld];
+        A[j + (size_t)c * ld] = A[p + (size_t)c * ld];
+        A[p + (size_t)c * ld] = t;
+      }
+    __syncthreads();
+    double piv = A[j + (size_t)j * ld];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (size_t)j * ld] /= piv;
+    __syncthreads();
+    int w = kend - j - 1, h = n - j - 1;
+    for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
+      int i = j + 1 + e % h, c = j + 1 + e / h;
+      A[i + (size_t)c * ld] -= A[i + (size_t)j * ld] * A[j + (size_t)c * ld];
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^-1 A12 for the columns right of the panel; grid (colchunks, items)
+static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int k0) {
+  LuItem it = items[blockIdx.y];
+  int n = it.n;
+  int kend = min(n, k0 + LU_NB);
+  int c = kend + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n || c >= n) return;
+  double* A = it.a;
+  const int ld = it.ld;
+  double x[LU_NB];
+  for (int j = k0; j < kend; ++j) x[j - k0] = A[j + (size_t)c * ld];
+  for (int j = k0; j < kend; ++j) {
+    double xj = x[j - k0];
+    for (int i = j + 1; i < kend; ++i) x[i - k0] -= A[i + (size_t)j * ld] * xj;
+  }
+  for (int j = k0; j < kend; ++j) A[j + (size_t)c * ld] = x[j - k0];
+}
+
+// 64x64 FP64 tile: C[i0.., j0..] += alpha * A[i0.., 0..K) * B[0..K, j0..]
+// (A column-major lda, B column-major ldb, C column-major ldc), bounds
+// rows < mr, cols < nc.  256 threads, 4x4 outputs each.
+__device__ inline void tile_gemm_64(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                    int mr, int nc, int K, double alpha) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int kk = e >> 6, ii = e & 63;
+      As[kk][ii] = (ii < mr && k0 + kk < K) ? A[ii + (size_t)(k0 + kk) * lda] : 0.0;
+      int jj = e >> 4, k2 = e & 15;
+      Bs[k2][jj] = (jj < nc && k0 + k2 < K) ? B[(k0 + k2) + (size_t)jj * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc[a][b];
+    }
+}
+
+// A22 -= L21 U12 ; grid (coltiles, rowtiles, items)
+static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int k0) {
+  LuItem it = items[blockIdx.z];
+  int n = it.n;
+  int kend = min(n, k0 + LU_NB);
+  int i0 = kend + blockIdx.y * 64, j0 = kend + blockIdx.x * 64;
+  if (k0 >= n || i0 >= n || j0 >= n) return;
+  double* A = it.a;
+  const int ld = it.ld;
+  tile_gemm_64(A + i0 + (size_t)k0 * ld, ld, A + k0 + (size_t)j0 * ld, ld, A + i0 + (size_t)j0 * ld, ld,
+               n - i0, n - j0, kend - k0, -1.0);
+}
+
+// X := A^-1 X for an LU-factored A (ipiv interchanges, unit L, U) on a strip
+// of up to 32 right-hand-side columns; grid (strips, items).  X column-major
+// with leading dimension ldx, ncols columns, per item.
+struct SolveItem {
+  const double* a;
+  const int* ipiv;
+  int n, ld;
+  double* x;
+  int ldx, ncols;
+};
+
+static __global__ void __launch_bounds__(256) k_lu_solve_strip(const SolveItem* items) {
+  SolveItem it = items[blockIdx.y];
+  int c0 = blockIdx.x * 32;
+  if (c0 >= it.ncols || it.n == 0) return;
+  int nc = min(32, it.ncols - c0);
+  int n = it.n;
+  const double* A = it.a;
+  const int ld = it.ld;
+  double* X = it.x + (size_t)c0 * it.ldx;
+  const int ldx = it.ldx;
+  int lane = threadIdx.x & 31, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
+  // interchanges
+  if (grp == 0 && lane < nc)
+    for (int k = 0; k < n; ++k) {
+      int p = it.ipiv[k];
+      if (p != k) {
+        double t = X[k + (size_t)lane * ldx];
+        X[k + (size_t)lane * ldx] = X[p + (size_t)lane * ldx];
+        X[p + (size_t)lane * ldx] = t;
+      }
+    }
+  __syncthreads();
+  // forward: unit lower
+  for (int k = 0; k < n; ++k) {
+    double xk = lane < nc ? X[k + (size_t)lane * ldx] : 0.0;
+    for (int i = k + 1 + grp; i < n; i += ngrp)
+      if (lane < nc) X[i + (size_t)lane * ldx] -= A[i + (size_t)k * ld] * xk;
+    __syncthreads();
+  }
+  // backward: upper
+  for (int k = n - 1; k >= 0; --k) {
+    if (grp == 0 && lane < nc) X[k + (size_t)lane * ldx] /= A[k + (size_t)k * ld];
+    __syncthreads();
+    double xk = lane < nc ? X[k + (size_t)lane * ldx] : 0.0;
+    for (int i = grp; i < k; i += ngrp)
+      if (lane < nc) X[i + (size_t)lane * ldx] -= A[i + (size_t)k * ld] * xk;
+    __syncthreads();
+  }
+}
+
+// column maxima of |A| (n x n), one block per item
+static __global__ void k_colmax(const LuItem* items, double* out, int stride) {
+  LuItem it = items[blockIdx.x];
+  for (int c = threadIdx.x; c < it.n; c += blockDim.x) {
+    double mx = 0.0;
+    for (int i = 0; i < it.n; ++i) mx = fmax(mx, fabs(it.a[i + (size_t)c * it.ld]));
+    out[(size_t)blockIdx.x * stride + c] = mx;
+  }
+}
+
+}  // namespace aifmm

@@ -1,0 +1,1200 @@
+// AIFMM elimination on the GPU (Sec. 3.2-3.5, Algorithm 2).
+//
+// Level l (L down to 2) holds, per box b, the particle equations X_b, the
+// multipole equation Y_b and the locals equation Lc_b (Sec. 3.1).  The boxes
+// of a level are eliminated in distance-2 colour order: boxes of one colour
+// have disjoint neighbourhoods, so each colour is one batch.  Per colour:
+//   1. compress and redirect every pending well-separated fill-in of each box
+//      (Sec. 3.2.1-3.2.3; Algorithm 2 compresses a fill-in once, just before
+//      one of its boxes is eliminated): RRQR of [U_b | row fill-ins] and
+//      [V_b | column fill-ins^T] with the existing basis taken first, ranks
+//      made equal, the locals row of b multiplied by L_b = U~^T U_b (other
+//      M2L and L2L updates), the multipole column of b by R_b^T = (V~^T V_b)^T
+//      (other M2L and M2M updates), M2P/P2L fill-ins added to the M2L, P2P
+//      fill-ins turned into P2L / M2P fill-ins of the partner;
+//   2. LU (partial pivoting) of the pivot block [[K_bb, U_b], [V_b^T, 0]];
+//   3. Z = Piv^-1 [coupled columns]; Schur update of every coupled block
+//      (P2P, M2P, P2L, M2L fill-ins, Table Notations), flagging blocks between
+//      well-separated boxes as pending.
+// Then the level transition builds level l-1 from the locals rows and the
+// multipole columns (eqs. particleAtNonLeafLevel, EqXl2), and after level 2
+// the dense level-1 system is factored.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
+#include "dense.cuh"
+#include "internal.h"
+#include "level.cuh"
+
+namespace aifmm {
+
+namespace {
+
+LV view(Handle& h, FacLevel& F) {
+  LV v;
+  v.l = F.l;
+  v.d = h.d;
+  v.n = F.n;
+  v.nb = F.nb;
+  v.M = F.M;
+  v.R = F.R;
+  v.P = F.P;
+  v.Rp = F.Rp;
+  v.ns5 = F.ns5;
+  v.ns6 = F.ns6;
+  v.m = F.m;
+  v.r = F.r;
+  v.XX = F.XX;
+  v.XY = F.XY;
+  v.LX = F.LX;
+  v.LY = F.LY;
+  v.U = F.U;
+  v.V = F.V;
+  v.Ud = F.Ud;
+  v.Vd = F.Vd;
+  v.LU = F.LU;
+  v.ipiv = F.ipiv;
+  v.flag = F.flag;
+  return v;
+}
+
+// ============================ level setup ====================================
+
+// leaf near field K_bq for q in N(b); grid (nb, 3^d)
+__global__ void k_setup_leaf_K(LV v, const int* __restrict__ start, KParams kp, Pts P) {
+  int b = blockIdx.x;
+  int c[3], q[3];
+  morton_coords(b, v.d, v.l, c);
+  int o = blockIdx.y;
+  for (int k = 0; k < 3; ++k) q[k] = c[k];
+  int oo = o;
+  for (int k = 0; k < v.d; ++k) {
+    q[k] = c[k] + (oo % 3) - 1;
+    oo /= 3;
+  }
+  if (!in_grid(q, v.d, v.n)) return;
+  int qb = morton_key(q, v.d, v.l);
+  int s = slot5(c, q, v.d);
+  int sb = start[b], mb = start[b + 1] - sb;
+  int sq = start[qb], mq = start[qb + 1] - sq;
+  double* K = v.xx(b, s);
+  for (int e = threadIdx.x; e < mb * mq; e += blockDim.x) {
+    int i = e % mb, j = e / mb;
+    K[i + (size_t)j * v.M] = keval(kp, P, sb + i, sq + j);
+  }
+}
+
+// M2L blocks A_bd = A(t^{b,i}, t^{d,i}) for d in IL(b); grid (nb, ns6)
+__global__ void k_setup_m2l(LV v, const int* __restrict__ pivpos, int nR, KParams kp, Pts P) {
+  int b = blockIdx.x, s = blockIdx.y;
+  int c[3], q[3];
+  morton_coords(b, v.d, v.l, c);
+  slot6_coords(c, s, v.d, q);
+  if (!in_grid(q, v.d, v.n) || cheb(c, q, v.d) <= 1) return;
+  int qb = morton_key(q, v.d, v.l);
+  int rb = v.r[b], rq = v.r[qb];
+  double* A = v.ly(b, s);
+  const int* tb = pivpos + (size_t)b * nR;
+  const int* tq = pivpos + (size_t)qb * nR;
+  for (int e = threadIdx.x; e < rb * rq; e += blockDim.x) {
+    int i = e % rb, j = e / rb;
+    A[i + (size_t)j * v.R] = keval(kp, P, tb[i], tq[j]);
+  }
+}
+
+// U^dag_b / V^dag_b (level l >= 3): rows of the parent's NNCA basis that belong
+// to child b; grid nb
+__global__ void k_setup_udag(LV v, const double* __restrict__ pU, int pM, int pR, const int* __restrict__ prank,
+                             const int* __restrict__ crank0) {
+  int b = blockIdx.x;
+  int Pb = b >> v.d;
+  int off = 0;
+  for (int c = Pb << v.d; c < b; ++c) off += crank0[c];
+  int rb = crank0[b], rp = prank[Pb];
+  const double* src = pU + (size_t)Pb * pM * pR;
+  double* Ud = v.ud(b);
+  double* Vd = v.vd(b);
+  for (int e = threadIdx.x; e < rb * rp; e += blockDim.x) {
+    int i = e % rb, j = e / rb;
+    double x = src[(off + i) + (size_t)j * pM];
+    Ud[i + (size_t)j * v.R] = x;
+    Vd[i + (size_t)j * v.R] = x;
+  }
+}
+
+// non-leaf: K^{(l)}_{PQ} from the level-(l+1) locals/multipole blocks, and
+// U_P, V_P stacked from the children's U^dag, V^dag; grid (nb, 3^d)
+__global__ void k_setup_parent(LV v, LV c, const int* __restrict__ cxoff) {
+  int Pb = blockIdx.x;
+  int pc[3], qc[3];
+  morton_coords(Pb, v.d, v.l, pc);
+  int o = blockIdx.y;
+  for (int k = 0; k < 3; ++k) qc[k] = pc[k];
+  int oo = o;
+  for (int k = 0; k < v.d; ++k) {
+    qc[k] = pc[k] + (oo % 3) - 1;
+    oo /= 3;
+  }
+  if (!in_grid(qc, v.d, v.n)) return;
+  int Qb = morton_key(qc, v.d, v.l);
+  int s = slot5(pc, qc, v.d);
+  double* K = v.xx(Pb, s);
+  int nch = 1 << v.d;
+  for (int a = 0; a < nch; ++a) {
+    int ca = (Pb << v.d) + a;
+    int ra = c.r[ca], oa = cxoff[ca];
+    int cca[3];
+    morton_coords(ca, v.d, c.l, cca);
+    for (int bq = 0; bq < nch; ++bq) {
+      int cb = (Qb << v.d) + bq;
+      int rbq = c.r[cb], ob = cxoff[cb];
+      int ccb[3];
+      morton_coords(cb, v.d, c.l, ccb);
+      int s6 = slot6(cca, ccb, v.d);
+      const double* src = c.ly(ca, s6);
+      for (int e = threadIdx.x; e < ra * rbq; e += blockDim.x) {
+        int i = e % ra, j = e / ra;
+        K[(oa + i) + (size_t)(ob + j) * v.M] = src[i + (size_t)j * c.R];
+      }
+    }
+  }
+  if (o == (ipow(3, v.d) - 1) / 2) {  // centre: stack U^dag and V^dag
+    int rp = v.r[Pb];
+    for (int a = 0; a < nch; ++a) {
+      int ca = (Pb << v.d) + a;
+      int ra = c.r[ca], oa = cxoff[ca];
+      const double* su = c.ud(ca);
+      const double* sv = c.vd(ca);
+      for (int e = threadIdx.x; e < ra * rp; e += blockDim.x) {
+        int i = e % ra, j = e / ra;
+        v.u(Pb)[(oa + i) + (size_t)j * v.M] = su[i + (size_t)j * c.R];
+        v.v(Pb)[(oa + i) + (size_t)j * v.M] = sv[i + (size_t)j * c.R];
+      }
+    }
+  }
+}
+
+__global__ void k_copy_basis(LV v, const double* __restrict__ nU, int nM, int nR) {
+  int b = blockIdx.x;
+  int mb = v.m[b], rb = v.r[b];
+  const double* src = nU + (size_t)b * nM * nR;
+  for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
+    int i = e % mb, j = e / mb;
+    double x = src[i + (size_t)j * nM];
+    v.u(b)[i + (size_t)j * v.M] = x;
+    v.v(b)[i + (size_t)j * v.M] = x;
+  }
+}
+
+// ============================ compress and redirect ===========================
+
+struct Cmp {
+  int col, cnt;        // colour, boxes in the colour
+  int WC;              // column capacity of the gather workspaces
+  double* W;           // [cnt][2][M*WC] gather + Householder workspace
+  double* Q;           // [cnt][2][M*M]  bases U~ (side 0) and V~ (side 1)
+  double* cn;          // [cnt][2][WC]   residual column norms^2
+  int* nc;             // [cnt][2] gathered columns
+  int* rk;             // [cnt][2] own ranks
+  int* rn;             // [cnt] equalised rank
+  int* rold;           // [cnt] rank before compression
+  int* skip;           // [cnt] 1 if nothing is pending
+  double* Lm;          // [cnt][2][R*R] L_b (side 0), R_b (side 1), ld R
+  double eps;
+};
+
+// fill-in flags are read with a load that bypasses the non-coherent cache
+// path; they are only ever modified with atomics
+__device__ inline unsigned ldflag(const unsigned* p) { return __ldcg(p); }
+
+__device__ inline int cbox(const Cmp& c, const LV& v, int t) { return colour_box(c.col, t, v.d, v.l); }
+
+// pending well-separated fill-in of box b at stencil slot s, for one side:
+// side 0 -> the block in row X_b (P2P_bq in XX if q is not yet eliminated,
+// M2P_bq in XY if it is); side 1 -> the block in column x_b of the partner's
+// row (P2P_qb in XX, or P2L_qb in LX), gathered transposed.
+struct WsBlk {
+  const double* src;
+  int ld, rows, cols, ok;
+};
+
+__device__ __noinline__ WsBlk ws_block(const LV v, int b, int s, int side, int col) {
+  WsBlk w;
+  w.src = nullptr;
+  w.ld = w.rows = w.cols = w.ok = 0;
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  slot5_coords(bc, s, v.d, q);
+  if (!in_grid(q, v.d, v.n) || cheb(bc, q, v.d) != 2) return w;
+  int qb = morton_key(q, v.d, v.l);
+  bool elim = colour_of(q, v.d) < col;
+  if (side == 0) {
+    if (!(ldflag(v.flag + (size_t)b * v.ns5 + s) & 1u)) return w;
+    w.src = elim ? v.xy(b, s) : v.xx(b, s);
+    w.ld = v.M;
+    w.rows = v.m[b];
+    w.cols = elim ? v.r[qb] : v.m[qb];
+  } else {
+    int sq = slot5(q, bc, v.d);
+    unsigned f = ldflag(v.flag + (size_t)qb * v.ns5 + sq);
+    if (elim) {
+      if (!(f & 2u)) return w;
+      w.src = v.lx(qb, sq);
+      w.ld = v.R;
+      w.rows = v.r[qb];
+    } else {
+      if (!(f & 1u)) return w;
+      w.src = v.xx(qb, sq);
+      w.ld = v.M;
+      w.rows = v.m[qb];
+    }
+    w.cols = v.m[b];
+  }
+  w.ok = 1;
+  return w;
+}
+
+// gather [U_b | row fill-ins] (side 0) and [V_b | column fill-ins^T] (side 1)
+// grid (cnt, 2)
+__global__ void k_cmp_gather(LV v, Cmp c) {
+  __shared__ WsBlk list[128];
+  __shared__ int offs[128];
+  __shared__ int nlist, total;
+  int t = blockIdx.x, side = blockIdx.y;
+  int b = cbox(c, v, t);
+  int mb = v.m[b], rb = v.r[b];
+  double* W = c.W + ((size_t)t * 2 + side) * v.M * c.WC;
+  if (threadIdx.x == 0) {
+    int nl = 0, off = rb;
+    for (int s = 0; s < v.ns5 && nl < 128; ++s) {
+      WsBlk w = ws_block(v, b, s, side, c.col);
+      if (!w.ok) continue;
+      list[nl] = w;
+      offs[nl] = off;
+      off += side == 0 ? w.cols : w.rows;
+      ++nl;
+    }
+    nlist = nl;
+    total = off;
+  }
+  __syncthreads();
+  const double* base = side == 0 ? v.u(b) : v.v(b);
+  for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
+    int i = e % mb, j = e / mb;
+    W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
+  }
+  for (int k = 0; k < nlist; ++k) {
+    WsBlk w = list[k];
+    int off = offs[k];
+    for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
+      int i = e % w.rows, j = e / w.rows;
+      if (side == 0) W[i + (size_t)(off + j) * v.M] = w.src[i + (size_t)j * w.ld];
+      else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
+    }
+  }
+  if (threadIdx.x == 0) {
+    c.nc[t * 2 + side] = total;
+    if (side == 0) c.rold[t] = rb;
+  }
+}
+
+__global__ void k_cmp_skip(LV v, Cmp c) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= c.cnt) return;
+  int b = cbox(c, v, t);
+  int rb = v.r[b];
+  c.skip[t] = (v.m[b] == 0 || (c.nc[2 * t] == rb && c.nc[2 * t + 1] == rb)) ? 1 : 0;
+}
+
+// Householder QR with column pivoting; the first nf = r_b columns are taken
+// in order, then the largest residual column among the fill-ins while its
+// norm exceeds eps * max_j ||F_j||.  Produces Q[:, :rank] explicitly.
+// grid (cnt, 2), 512 threads.
+__global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
+  __shared__ double shv[32];
+  __shared__ int shi[32];
+  __shared__ double shs[32];
+  int t = blockIdx.x, side = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  const int m = v.m[b], n = c.nc[t * 2 + side], nf = c.rold[t];
+  const int M = v.M;
+  double* W = c.W + ((size_t)t * 2 + side) * M * c.WC;
+  double* cn = c.cn + ((size_t)t * 2 + side) * c.WC;
+  double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // initial column norms and the threshold
+  double mx = 0.0;
+  for (int j = nf + w; j < n; j += nw) {
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc += W[i + (size_t)j * M] * W[i + (size_t)j * M];
+    acc = warp_sum(acc);
+    if (lane == 0) cn[j] = acc;
+    mx = fmax(mx, acc);
+  }
+  // block max of mx
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if (lane == 0) shs[w] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < nw; ++q) a = fmax(a, shs[q]);
+    shs[0] = a;
+  }
+  __syncthreads();
+  const double tau = c.eps * sqrt(shs[0]);
+  __syncthreads();
+  const int kmax = min(m, n);
+  int k = 0;
+  for (; k < kmax; ++k) {
+    if (k >= nf) {
+      ArgMax best;
+      best.v = -1.0;
+      best.i = -1;
+      for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
+        ArgMax x;
+        x.v = cn[j];
+        x.i = j;
+        best = amax_pick(best, x);
+      }
+      best = block_amax(best, shv, shi);
+      if (!(sqrt(fmax(best.v, 0.0)) > tau)) break;
+      int p = best.i;
+      if (p != k) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          double x = W[i + (size_t)k * M];
+          W[i + (size_t)k * M] = W[i + (size_t)p * M];
+          W[i + (size_t)p * M] = x;
+        }
+        if (threadIdx.x == 0) {
+          double x = cn[k];
+          cn[k] = cn[p];
+          cn[p] = x;
+        }
+      }
+      __syncthreads();
+    }
+    // reflector from W[k:m, k]
+    double acc = 0.0;
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) acc += W[i + (size_t)k * M] * W[i + (size_t)k * M];
+    double a2 = block_sum(acc, shs);
+    double alpha = sqrt(a2);
+    double x0 = W[k + (size_t)k * M];
+    __syncthreads();
+    if (alpha == 0.0) {
+      // identity reflector: mark with a zero vector
+      for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
+    // ||v||^2 = a2 - x0^2 + v0^2
+    double nv = sqrt(a2 - x0 * x0 + v0 * v0);
+    if (threadIdx.x == 0) W[k + (size_t)k * M] = v0;
+    __syncthreads();
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] /= nv;
+    __syncthreads();
+    // apply to the trailing columns and refresh their residual norms
+    for (int j = k + 1 + w; j < n; j += nw) {
+      double dt = 0.0;
+      for (int i = k + lane; i < m; i += 32) dt += W[i + (size_t)k * M] * W[i + (size_t)j * M];
+      dt = warp_sum(dt);
+      double nn = 0.0;
+      for (int i = k + lane; i < m; i += 32) {
+        double x = W[i + (size_t)j * M] - 2.0 * dt * W[i + (size_t)k * M];
+        W[i + (size_t)j * M] = x;
+        if (i > k) nn += x * x;
+      }
+      nn = warp_sum(nn);
+      if (lane == 0) cn[j] = nn;
+    }
+    __syncthreads();
+  }
+  const int rank = k;
+  // form Q[:, :rank] = H_0 ... H_{rank-1} [e_0 .. e_{rank-1}]
+  for (int j = w; j < rank; j += nw) {
+    double* y = Q + (size_t)j * M;
+    for (int i = lane; i < m; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int kk = rank - 1; kk >= 0; --kk) {
+      double dt = 0.0;
+      for (int i = kk + lane; i < m; i += 32) dt += W[i + (size_t)kk * M] * y[i];
+      dt = warp_sum(dt);
+      for (int i = kk + lane; i < m; i += 32) y[i] -= 2.0 * dt * W[i + (size_t)kk * M];
+      __syncwarp();
+    }
+  }
+  if (threadIdx.x == 0) c.rk[t * 2 + side] = rank;
+}
+
+// equal ranks: the smaller side takes the other side's extra basis columns,
+// orthogonalised against its own by a Householder QR with every column forced.
+// grid cnt, 256 threads.  Uses the side's W workspace as scratch.
+__global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
+  __shared__ double shs[32];
+  int t = blockIdx.x;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  const int m = v.m[b], M = v.M;
+  int rU = c.rk[2 * t], rV = c.rk[2 * t + 1];
+  int rn = max(rU, rV);
+  if (threadIdx.x == 0) c.rn[t] = rn;
+  for (int side = 0; side < 2; ++side) {
+    int k = side == 0 ? rU : rV;
+    if (k >= rn) continue;
+    double* Qs = c.Q + ((size_t)t * 2 + side) * M * M;
+    const double* Qo = c.Q + ((size_t)t * 2 + (1 - side)) * M * M;
+    double* A = c.W + ((size_t)t * 2 + side) * M * c.WC;   // m x rn
+    for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
+      int i = e % m, j = e / m;
+      A[i + (size_t)j * M] = j < k ? Qs[i + (size_t)j * M] : Qo[i + (size_t)j * M];
+    }
+    __syncthreads();
+    for (int kk = 0; kk < rn; ++kk) {
+      double acc = 0.0;
+      for (int i = kk + threadIdx.x; i < m; i += blockDim.x) acc += A[i + (size_t)kk * M] * A[i + (size_t)kk * M];
+      double a2 = block_sum(acc, shs);
+      double alpha = sqrt(a2);
+      double x0 = A[kk + (size_t)kk * M];
+      __syncthreads();
+      if (alpha == 0.0) {
+        for (int i = kk + threadIdx.x; i < m; i += blockDim.x) A[i + (size_t)kk * M] = 0.0;
+        __syncthreads();
+        continue;
+      }
+      double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
+      double nv = sqrt(a2 - x0 * x0 + v0 * v0);
+      if (threadIdx.x == 0) A[kk + (size_t)kk * M] = v0;
+      __syncthreads();
+      for (int i = kk + threadIdx.x; i < m; i += blockDim.x) A[i + (size_t)kk * M] /= nv;
+      __syncthreads();
+      int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int j = kk + 1 + w; j < rn; j += nw) {
+        double dt = 0.0;
+        for (int i = kk + lane; i < m; i += 32) dt += A[i + (size_t)kk * M] * A[i + (size_t)j * M];
+        dt = warp_sum(dt);
+        for (int i = kk + lane; i < m; i += 32) A[i + (size_t)j * M] -= 2.0 * dt * A[i + (size_t)kk * M];
+      }
+      __syncthreads();
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = w; j < rn; j += nw) {
+      double* y = Qs + (size_t)j * M;
+      for (int i = lane; i < m; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+      __syncwarp();
+      for (int kk = rn - 1; kk >= 0; --kk) {
+        double dt = 0.0;
+        for (int i = kk + lane; i < m; i += 32) dt += A[i + (size_t)kk * M] * y[i];
+        dt = warp_sum(dt);
+        for (int i = kk + lane; i < m; i += 32) y[i] -= 2.0 * dt * A[i + (size_t)kk * M];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R
+__global__ void k_cmp_lmat(LV v, Cmp c) {
+  int t = blockIdx.x, side = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  const int m = v.m[b], M = v.M, rn = c.rn[t], ro = c.rold[t];
+  const double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
+  const double* B = side == 0 ? v.u(b) : v.v(b);
+  double* Lm = c.Lm + ((size_t)t * 2 + side) * v.R * v.R;
+  for (int e = threadIdx.x; e < rn * ro; e += blockDim.x) {
+    int i = e % rn, j = e / rn;
+    double acc = 0.0;
+    for (int p = 0; p < m; ++p) acc += Q[p + (size_t)i * M] * B[p + (size_t)j * M];
+    Lm[i + (size_t)j * v.R] = acc;
+  }
+}
+
+// row side: every block of the locals row of b is multiplied by L_b
+// (the other-M2L and L2L updates); grid (ns6 + 1, cnt)
+__global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
+  __shared__ double col[1024];
+  int s = blockIdx.x, t = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  const int rn = c.rn[t], ro = c.rold[t];
+  const double* Lm = c.Lm + ((size_t)t * 2) * v.R * v.R;
+  double* blk;
+  int ncols;
+  if (s < v.ns6) {
+    int bc[3], q[3];
+    morton_coords(b, v.d, v.l, bc);
+    slot6_coords(bc, s, v.d, q);
+    if (!in_grid(q, v.d, v.n)) return;
+    int qb = morton_key(q, v.d, v.l);
+    blk = v.ly(b, s);
+    ncols = v.r[qb];
+  } else {
+    if (v.l < 3) return;
+    blk = v.ud(b);
+    ncols = v.Rp;  // all parent columns (zeros beyond the parent's rank)
+  }
+  for (int j = 0; j < ncols; ++j) {
+    double* cj = blk + (size_t)j * v.R;
+    for (int i = threadIdx.x; i < ro; i += blockDim.x) col[i] = cj[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < rn; i += blockDim.x) {
+      double acc = 0.0;
+      for (int p = 0; p < ro; ++p) acc += Lm[i + (size_t)p * v.R] * col[p];
+      cj[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// row side fill-ins: M2P_bq -> A_bq += U~^T M2P_bq ; P2P_bq -> P2L_bq = U~^T P2P_bq
+// then the fill-in block is cleared.  grid (ns5, cnt)
+__global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c) {
+  int s = blockIdx.x, t = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  int bc[3];
+  morton_coords(b, v.d, v.l, bc);
+  __shared__ WsBlk sw;
+  if (threadIdx.x == 0) sw = ws_block(v, b, s, 0, c.col);
+  __syncthreads();
+  if (!sw.ok) return;
+  const double* src = sw.src;
+  const int ld = sw.ld, rows = sw.rows, cols = sw.cols;
+  int q[3];
+  slot5_coords(bc, s, v.d, q);
+  bool elim = colour_of(q, v.d) < c.col;
+  const int m = rows, M = v.M, rn = c.rn[t];
+  const double* Q = c.Q + ((size_t)t * 2) * M * M;
+  double* dst;
+  if (elim) dst = v.ly(b, slot6(bc, q, v.d));
+  else dst = v.lx(b, s);
+  double* srcw = const_cast<double*>(src);
+  for (int e = threadIdx.x; e < rn * cols; e += blockDim.x) {
+    int i = e % rn, j = e / rn;
+    double acc = 0.0;
+    for (int p = 0; p < m; ++p) acc += Q[p + (size_t)i * M] * src[p + (size_t)j * ld];
+    if (elim) dst[i + (size_t)j * v.R] += acc;
+    else dst[i + (size_t)j * v.R] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * cols; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    srcw[i + (size_t)j * ld] = 0.0;
+  }
+}
+
+// flags after the row side, U_b := U~, r_b := rn ; grid cnt
+__global__ void k_cmp_row_done(LV v, Cmp c) {
+  int t = blockIdx.x;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (threadIdx.x == 0)
+    for (int s = 0; s < v.ns5; ++s) {
+      slot5_coords(bc, s, v.d, q);
+      if (!in_grid(q, v.d, v.n) || cheb(bc, q, v.d) != 2) continue;
+      unsigned* f = v.flag + (size_t)b * v.ns5 + s;
+      if (ldflag(f) & 1u) {
+        atomicAnd(f, ~1u);
+        if (colour_of(q, v.d) > c.col) atomicOr(f, 2u);   // a new P2L_bq waits for q's column side
+      }
+    }
+  const double* Q = c.Q + ((size_t)t * 2) * M * M;
+  for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    v.u(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
+  }
+  if (threadIdx.x == 0) v.r[b] = rn;
+}
+
+// column side: every block of the multipole column of b is multiplied by
+// R_b^T (other-M2L and M2M updates); grid (ns6 + 1, cnt)
+__global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
+  __shared__ double row[1024];
+  int s = blockIdx.x, t = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  const int rn = c.rn[t], ro = c.rold[t];
+  const double* Rm = c.Lm + ((size_t)t * 2 + 1) * v.R * v.R;
+  int bc[3];
+  morton_coords(b, v.d, v.l, bc);
+  if (s < v.ns6) {
+    int q[3];
+    slot6_coords(bc, s, v.d, q);   // d in the window of b  <=>  b in the window of d
+    if (!in_grid(q, v.d, v.n)) return;
+    int db = morton_key(q, v.d, v.l);
+    int sd = slot6(q, bc, v.d);
+    double* blk = v.ly(db, sd);
+    int nrows = v.r[db];
+    for (int i = 0; i < nrows; ++i) {
+      for (int p = threadIdx.x; p < ro; p += blockDim.x) row[p] = blk[i + (size_t)p * v.R];
+      __syncthreads();
+      for (int j = threadIdx.x; j < rn; j += blockDim.x) {
+        double acc = 0.0;
+        for (int p = 0; p < ro; ++p) acc += row[p] * Rm[j + (size_t)p * v.R];
+        blk[i + (size_t)j * v.R] = acc;
+      }
+      __syncthreads();
+    }
+  } else {
+    if (v.l < 3) return;
+    // V^dag_b (V form, r_old x rp) := R_b V^dag_b ; column-wise
+    double* blk = v.vd(b);
+    for (int j = 0; j < v.Rp; ++j) {
+      double* cj = blk + (size_t)j * v.R;
+      for (int i = threadIdx.x; i < ro; i += blockDim.x) row[i] = cj[i];
+      __syncthreads();
+      for (int i = threadIdx.x; i < rn; i += blockDim.x) {
+        double acc = 0.0;
+        for (int p = 0; p < ro; ++p) acc += Rm[i + (size_t)p * v.R] * row[p];
+        cj[i] = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
+// grid (ns5, cnt)
+__global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c) {
+  int s = blockIdx.x, t = blockIdx.y;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  int bc[3];
+  morton_coords(b, v.d, v.l, bc);
+  __shared__ WsBlk sw;
+  if (threadIdx.x == 0) sw = ws_block(v, b, s, 1, c.col);
+  __syncthreads();
+  if (!sw.ok) return;
+  const double* src = sw.src;
+  const int ld = sw.ld, rows = sw.rows, cols = sw.cols;
+  int q[3];
+  slot5_coords(bc, s, v.d, q);
+  int qb = morton_key(q, v.d, v.l);
+  bool elim = colour_of(q, v.d) < c.col;
+  const int M = v.M, rn = c.rn[t];
+  const double* Q = c.Q + ((size_t)t * 2 + 1) * M * M;
+  double* dst;
+  int ldd;
+  if (elim) {
+    dst = v.ly(qb, slot6(q, bc, v.d));
+    ldd = v.R;
+  } else {
+    dst = v.xy(qb, slot5(q, bc, v.d));
+    ldd = v.M;
+  }
+  double* srcw = const_cast<double*>(src);
+  // src is rows x cols (cols = m_b); out rows x rn
+  for (int e = threadIdx.x; e < rows * rn; e += blockDim.x) {
+    int i = e % rows, j = e / rows;
+    double acc = 0.0;
+    for (int p = 0; p < cols; ++p) acc += src[i + (size_t)p * ld] * Q[p + (size_t)j * M];
+    if (elim) dst[i + (size_t)j * ldd] += acc;
+    else dst[i + (size_t)j * ldd] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+    int i = e % rows, j = e / rows;
+    srcw[i + (size_t)j * ld] = 0.0;
+  }
+}
+
+// flags after the column side (P2L consumed; P2P became a pending M2P of the
+// partner, which keeps bit 0) and V_b := V~ ; grid cnt
+__global__ void k_cmp_col_done(LV v, Cmp c) {
+  int t = blockIdx.x;
+  if (c.skip[t]) return;
+  int b = cbox(c, v, t);
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (threadIdx.x == 0)
+    for (int s = 0; s < v.ns5; ++s) {
+      slot5_coords(bc, s, v.d, q);
+      if (!in_grid(q, v.d, v.n) || cheb(bc, q, v.d) != 2) continue;
+      if (colour_of(q, v.d) < c.col) {
+        int qb = morton_key(q, v.d, v.l);
+        atomicAnd(v.flag + (size_t)qb * v.ns5 + slot5(q, bc, v.d), ~2u);
+      }
+    }
+  const double* Q = c.Q + ((size_t)t * 2 + 1) * M * M;
+  for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    v.v(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
+  }
+}
+
+// ============================ pivot, Z and Schur =============================
+
+struct Elim {
+  int col, cnt;
+  int ncmax;           // capacity of stacked columns
+  Coupled* rows;       // [cnt][MAXC]
+  Coupled* cols;       // [cnt][MAXC]
+  int* nrow;           // [cnt]
+  int* ncol;           // [cnt]
+  int* totc;           // [cnt] stacked columns
+  double* Z;           // [cnt][P * ncmax], ld P
+  LuItem* lu;          // [cnt]
+  SolveItem* sv;       // [cnt]
+  double* colmax;      // [cnt][P]
+};
+
+// coupled rows / columns of every box of the colour and the LU / solve items
+__global__ void k_coupled(LV v, Elim e) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= e.cnt) return;
+  int b = colour_box(e.col, t, v.d, v.l);
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  int nr = 0, nc = 0, ro = 0, co = 0;
+  Coupled* R = e.rows + (size_t)t * MAXC;
+  Coupled* C = e.cols + (size_t)t * MAXC;
+  int n3 = ipow(3, v.d);
+  for (int o = 0; o < n3; ++o) {
+    int oo = o;
+    for (int k = 0; k < 3; ++k) q[k] = bc[k];
+    for (int k = 0; k < v.d; ++k) {
+      q[k] = bc[k] + (oo % 3) - 1;
+      oo /= 3;
+    }
+    if (!in_grid(q, v.d, v.n) || (q[0] == bc[0] && q[1] == bc[1] && q[2] == bc[2])) continue;
+    int qb = morton_key(q, v.d, v.l);
+    bool elim = colour_of(q, v.d) < e.col;
+    int sz = elim ? v.r[qb] : v.m[qb];
+    if (sz == 0) continue;
+    R[nr].box = qb;
+    R[nr].type = elim ? 1 : 0;
+    R[nr].size = sz;
+    R[nr].off = ro;
+    ++nr;
+    ro += sz;
+    C[nc].box = qb;
+    C[nc].type = elim ? 1 : 0;
+    C[nc].size = sz;
+    C[nc].off = co;
+    ++nc;
+    co += sz;
+  }
+  int rb = v.r[b], mb = v.m[b];
+  if (rb > 0) {
+    R[nr].box = b;
+    R[nr].type = 2;
+    R[nr].size = rb;
+    R[nr].off = ro;
+    ++nr;
+    C[nc].box = b;
+    C[nc].type = 2;
+    C[nc].size = rb;
+    C[nc].off = co;
+    ++nc;
+    co += rb;
+  }
+  e.nrow[t] = nr;
+  e.ncol[t] = nc;
+  e.totc[t] = co;
+  LuItem it;
+  it.a = v.lu(b);
+  it.ipiv = v.piv(b);
+  it.colmax = e.colmax + (size_t)t * v.P;
+  it.n = mb + rb;
+  it.ld = v.P;
+  e.lu[t] = it;
+  SolveItem si;
+  si.a = v.lu(b);
+  si.ipiv = v.piv(b);
+  si.n = mb + rb;
+  si.ld = v.P;
+  si.x = e.Z + (size_t)t * v.P * e.ncmax;
+  si.ldx = v.P;
+  si.ncols = co;
+  e.sv[t] = si;
+}
+
+// Piv = [[K_bb, U_b], [V_b^T, 0]] into the LU storage; grid cnt
+__global__ void k_piv_build(LV v, Elim e) {
+  int t = blockIdx.x;
+  int b = colour_box(e.col, t, v.d, v.l);
+  const int m = v.m[b], r = v.r[b], n = m + r, P = v.P, M = v.M;
+  double* A = v.lu(b);
+  const double* K = v.xx(b, v.centre5());
+  for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
+    int i = x % n, j = x / n;
+    double val;
+    if (i < m && j < m) val = K[i + (size_t)j * M];
+    else if (i < m) val = v.u(b)[i + (size_t)(j - m) * M];
+    else if (j < m) val = v.v(b)[j + (size_t)(i - m) * M];
+    else val = 0.0;
+    A[i + (size_t)j * P] = val;
+  }
+}
+
+// B = A[pivot rows, coupled columns]: [c_C; 0] for x_q / y_q, [0; -I] for y_b
+__global__ void k_z_build(LV v, Elim e) {
+  int t = blockIdx.y, ci = blockIdx.x;
+  if (ci >= e.ncol[t]) return;
+  int b = colour_box(e.col, t, v.d, v.l);
+  int bc[3], qc[3];
+  morton_coords(b, v.d, v.l, bc);
+  const int m = v.m[b], r = v.r[b], n = m + r, P = v.P;
+  Coupled C = e.cols[(size_t)t * MAXC + ci];
+  double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)C.off * P;
+  if (C.type == 2) {
+    for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
+      int i = x % n, j = x / n;
+      Z[i + (size_t)j * P] = (i - m == j) ? -1.0 : 0.0;
+    }
+    return;
+  }
+  morton_coords(C.box, v.d, v.l, qc);
+  int s = slot5(bc, qc, v.d);
+  const double* src = C.type == 0 ? v.xx(b, s) : v.xy(b, s);
+  for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
+    int i = x % n, j = x / n;
+    Z[i + (size_t)j * P] = i < m ? src[i + (size_t)j * v.M] : 0.0;
+  }
+}
+
+// Schur update of every coupled block; 64x64 tiles.
+// grid (MAXC * tpb, MAXC * tpb, cnt) with tpb = tiles per block side.
+__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb) {
+  int t = blockIdx.z;
+  int ri = blockIdx.y / tpb, ti = blockIdx.y % tpb;
+  int cj = blockIdx.x / tpb, tj = blockIdx.x % tpb;
+  if (ri >= e.nrow[t] || cj >= e.ncol[t]) return;
+  Coupled R = e.rows[(size_t)t * MAXC + ri];
+  Coupled C = e.cols[(size_t)t * MAXC + cj];
+  int i0 = ti * 64, j0 = tj * 64;
+  if (i0 >= R.size || j0 >= C.size) return;
+  int b = colour_box(e.col, t, v.d, v.l);
+  const int m = v.m[b], P = v.P;
+  int bc[3], pc[3], qc[3];
+  morton_coords(b, v.d, v.l, bc);
+  morton_coords(R.box, v.d, v.l, pc);
+  morton_coords(C.box, v.d, v.l, qc);
+  const double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)(C.off + j0) * P;
+  // target block
+  double* T;
+  int ldt;
+  bool colx = C.type == 0;
+  if (R.type == 0) {
+    int s = slot5(pc, qc, v.d);
+    T = colx ? v.xx(R.box, s) : v.xy(R.box, s);
+    ldt = v.M;
+  } else {
+    if (colx) {
+      T = v.lx(R.box, slot5(pc, qc, v.d));
+    } else {
+      T = v.ly(R.box, slot6(pc, qc, v.d));
+    }
+    ldt = v.R;
+  }
+  T += i0 + (size_t)j0 * ldt;
+  int mr = min(64, R.size - i0), nc = min(64, C.size - j0);
+  if (R.type == 2) {
+    // (Lc_b, C) += Z[m + i, C]
+    for (int x = threadIdx.x; x < mr * nc; x += blockDim.x) {
+      int i = x % mr, j = x / mr;
+      T[i + (size_t)j * ldt] += Z[m + i0 + i + (size_t)j * P];
+    }
+    return;
+  }
+  int sp = slot5(pc, bc, v.d);
+  const double* A = R.type == 0 ? v.xx(R.box, sp) : v.lx(R.box, sp);
+  int lda = R.type == 0 ? v.M : v.R;
+  tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
+  // a block between well-separated boxes is a pending fill-in unless both
+  // boxes are eliminated (an M2L fill-in, kept without compression)
+  if (threadIdx.x == 0 && ti == 0 && tj == 0 && C.type != 2 && !(R.type == 1 && C.type == 1) &&
+      cheb(pc, qc, v.d) == 2)
+    atomicOr(v.flag + (size_t)R.box * v.ns5 + slot5(pc, qc, v.d), R.type == 0 ? 1u : 2u);
+}
+
+// ============================ top (level-1 system) ===========================
+
+__global__ void k_top_assemble(LV v, const int* __restrict__ toff, double* __restrict__ T, int ntop) {
+  int b = blockIdx.x, s = blockIdx.y;
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  slot6_coords(bc, s, v.d, q);
+  if (!in_grid(q, v.d, v.n)) return;
+  int qb = morton_key(q, v.d, v.l);
+  int rb = v.r[b], rq = v.r[qb];
+  const double* src = v.ly(b, s);
+  int ob = toff[b], oq = toff[qb];
+  for (int x = threadIdx.x; x < rb * rq; x += blockDim.x) {
+    int i = x % rb, j = x / rb;
+    T[(ob + i) + (size_t)(oq + j) * ntop] = src[i + (size_t)j * v.R];
+  }
+}
+
+// xoff of each box inside its parent's particles: sum of earlier siblings' ranks
+__global__ void k_xoff(int nb, int d, const int* __restrict__ r, int* __restrict__ xoff) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  int off = 0;
+  for (int c = (b >> d) << d; c < b; ++c) off += r[c];
+  xoff[b] = off;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+static int alloc_level(Handle& h, FacLevel& F) {
+  const size_t nb = F.nb;
+  F.m = hnew<int>(h, nb);
+  F.r = hnew<int>(h, nb);
+  F.xoff = hnew<int>(h, nb);
+  F.XX = hnew<double>(h, nb * F.ns5 * F.M * F.M);
+  F.XY = hnew<double>(h, nb * F.ns5 * F.M * F.R);
+  F.LX = hnew<double>(h, nb * F.ns5 * F.R * F.M);
+  F.LY = hnew<double>(h, nb * F.ns6 * F.R * F.R);
+  F.U = hnew<double>(h, nb * F.M * F.R);
+  F.V = hnew<double>(h, nb * F.M * F.R);
+  F.Ud = hnew<double>(h, nb * F.R * std::max(1, F.Rp));
+  F.Vd = hnew<double>(h, nb * F.R * std::max(1, F.Rp));
+  F.LU = hnew<double>(h, nb * F.P * F.P, false);
+  F.ipiv = hnew<int>(h, nb * F.P);
+  F.flag = hnew<unsigned>(h, nb * F.ns5);
+  if (!F.m || !F.r || !F.xoff || !F.XX || !F.XY || !F.LX || !F.LY || !F.U || !F.V || !F.Ud || !F.Vd || !F.LU ||
+      !F.ipiv || !F.flag)
+    return HOOM;
+  F.bytes = sizeof(double) * nb *
+            ((size_t)F.ns5 * (F.M * F.M + 2 * F.M * F.R) + (size_t)F.ns6 * F.R * F.R + 2 * F.M * F.R +
+             2 * F.R * std::max(1, F.Rp) + (size_t)F.P * F.P);
+  return HOK;
+}
+
+static int setup_level(Handle& h, int l) {
+  const int d = h.d, L = h.L;
+  cudaStream_t st = h.stream;
+  FacLevel& F = h.fac[l];
+  F.l = l;
+  F.nb = 1 << (d * l);
+  F.n = 1 << l;
+  F.ns5 = ipow(5, d);
+  F.ns6 = ipow(6, d);
+  const NnLevel& N = h.nn[l];
+  F.h_m.assign(F.nb, 0);
+  if (l == L) {
+    F.h_m = N.h_m;
+  } else {
+    const FacLevel& C = h.fac[l + 1];
+    for (int b = 0; b < F.nb; ++b)
+      for (int c = 0; c < (1 << d); ++c) F.h_m[b] += C.h_r[(b << d) + c];
+  }
+  F.h_r = N.h_rank;
+  int M = 1;
+  for (int b = 0; b < F.nb; ++b) M = std::max(M, F.h_m[b]);
+  F.M = M;
+  F.R = M;              // a rank never exceeds the particle count of its box
+  F.P = F.M + F.R;
+  F.Rp = 1;
+  if (l >= 3) {
+    const NnLevel& Np = h.nn[l - 1];
+    for (int b = 0; b < Np.nb; ++b) F.Rp = std::max(F.Rp, Np.h_rank[b]);
+  }
+  if (F.R + 1 > 1024) {
+    h.err = "rank capacity above 1024 at level " + std::to_string(l);
+    return HCAPACITY;
+  }
+  int e = alloc_level(h, F);
+  if (e) return e;
+  h.max_m = std::max(h.max_m, F.M);
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(F.m, F.h_m.data(), sizeof(int) * F.nb, cudaMemcpyHostToDevice, st));
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(F.r, F.h_r.data(), sizeof(int) * F.nb, cudaMemcpyHostToDevice, st));
+  LV v = view(h, F);
+  const int n3 = ipow(3, d);
+  if (l == L) {
+    k_setup_leaf_K<<<dim3(F.nb, n3), 256, 0, st>>>(v, h.start + h.soff[L], h.kp, h.P());
+    k_copy_basis<<<F.nb, 256, 0, st>>>(v, N.U, N.M, N.R);
+  } else {
+    FacLevel& C = h.fac[l + 1];
+    LV vc = view(h, C);
+    k_setup_parent<<<dim3(F.nb, n3), 256, 0, st>>>(v, vc, C.xoff);
+  }
+  k_setup_m2l<<<dim3(F.nb, F.ns6), 128, 0, st>>>(v, N.pivpos, N.R, h.kp, h.P());
+  if (l >= 3) {
+    const NnLevel& Np = h.nn[l - 1];
+    k_setup_udag<<<F.nb, 128, 0, st>>>(v, Np.U, Np.M, Np.R, Np.rank, N.rank);
+  }
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  return HOK;
+}
+
+static int factor_level(Handle& h, int l) {
+  const int d = h.d;
+  cudaStream_t st = h.stream;
+  FacLevel& F = h.fac[l];
+  LV v = view(h, F);
+  const int ncol = ipow(3, d);
+  int nws = ipow(5, d) - ipow(3, d);
+  for (int col = 0; col < ncol; ++col) {
+    int cnt = colour_count(col, d, F.n);
+    if (cnt == 0) continue;
+    // ---- compress and redirect
+    Cmp c;
+    c.col = col;
+    c.cnt = cnt;
+    c.eps = h.tol;
+    c.WC = F.R + nws * F.M;
+    size_t wsz = (size_t)cnt * 2 * F.M * c.WC;
+    c.W = (double*)hscratch(h, 20, sizeof(double) * wsz);
+    c.Q = (double*)hscratch(h, 21, sizeof(double) * (size_t)cnt * 2 * F.M * F.M);
+    c.cn = (double*)hscratch(h, 22, sizeof(double) * (size_t)cnt * 2 * c.WC);
+    int* ib = (int*)hscratch(h, 23, sizeof(int) * (size_t)cnt * 8);
+    c.Lm = (double*)hscratch(h, 24, sizeof(double) * (size_t)cnt * 2 * F.R * F.R);
+    if (!c.W || !c.Q || !c.cn || !ib || !c.Lm) return HOOM;
+    c.nc = ib;
+    c.rk = ib + 2 * cnt;
+    c.rn = ib + 4 * cnt;
+    c.rold = ib + 5 * cnt;
+    c.skip = ib + 6 * cnt;
+    k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c);
+    k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c);
+    k_cmp_qrcp<<<dim3(cnt, 2), 512, 0, st>>>(v, c);
+    k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c);
+    k_cmp_lmat<<<dim3(cnt, 2), 256, 0, st>>>(v, c);
+    k_cmp_row_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c);
+    k_cmp_row_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c);
+    k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c);
+    k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c);
+    k_cmp_col_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c);
+    k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c);
+    // ---- pivot LU
+    Elim e;
+    e.col = col;
+    e.cnt = cnt;
+    e.ncmax = ncol * F.M + F.R;
+    e.rows = (Coupled*)hscratch(h, 25, sizeof(Coupled) * (size_t)cnt * MAXC);
+    e.cols = (Coupled*)hscratch(h, 26, sizeof(Coupled) * (size_t)cnt * MAXC);
+    int* eb = (int*)hscratch(h, 27, sizeof(int) * (size_t)cnt * 3);
+    e.Z = (double*)hscratch(h, 28, sizeof(double) * (size_t)cnt * F.P * e.ncmax);
+    e.lu = (LuItem*)hscratch(h, 29, sizeof(LuItem) * cnt);
+    e.sv = (SolveItem*)hscratch(h, 30, sizeof(SolveItem) * cnt);
+    e.colmax = (double*)hscratch(h, 31, sizeof(double) * (size_t)cnt * F.P);
+    if (!e.rows || !e.cols || !eb || !e.Z || !e.lu || !e.sv || !e.colmax) return HOOM;
+    e.nrow = eb;
+    e.ncol = eb + cnt;
+    e.totc = eb + 2 * cnt;
+    k_coupled<<<(cnt + 127) / 128, 128, 0, st>>>(v, e);
+    k_piv_build<<<cnt, 256, 0, st>>>(v, e);
+    k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P);
+    for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
+      k_lu_panel<<<cnt, 256, 0, st>>>(e.lu, k0, h.derr);
+      k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0);
+      int tiles = (F.P + 63) / 64;
+      k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+    }
+    // ---- Z = Piv^-1 B and the Schur update
+    k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e);
+    k_lu_solve_strip<<<dim3((e.ncmax + 31) / 32, cnt), 256, 0, st>>>(e.sv);
+    int tpb = (F.M + 63) / 64;
+    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb);
+    AIFMM_CUDA_TRY(h, cudaGetLastError());
+  }
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(F.h_r.data(), F.r, sizeof(int) * F.nb, cudaMemcpyDeviceToHost, st));
+  AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));
+  int er = check_derr(h);
+  if (er) {
+    h.err = "factorisation failed at level " + std::to_string(l) +
+            (er == DERR_SINGULAR ? ": singular pivot block" : " (device error " + std::to_string(er) + ")");
+    return er == DERR_SINGULAR ? HSINGULAR : HCAPACITY;
+  }
+  k_xoff<<<(F.nb + 127) / 128, 128, 0, st>>>(F.nb, d, F.r, F.xoff);
+  for (int b = 0; b < F.nb; ++b) h.max_rank_factor = std::max(h.max_rank_factor, F.h_r[b]);
+  return HOK;
+}
+
+// algorithmic FP64 flops of one level (pivot LU, Z and Schur), from the final
+// sizes; ranks of boxes eliminated later are their final ranks too, which is
+// what the Schur update saw (ranks change only at a box's own compression).
+static double level_flops(Handle& h, int l) {
+  const int d = h.d;
+  FacLevel& F = h.fac[l];
+  double fl = 0.0;
+  for (int b = 0; b < F.nb; ++b) {
+    int bc[3], q[3];
+    morton_coords(b, d, l, bc);
+    int cb = colour_of(bc, d);
+    double m = F.h_m[b], r = F.h_r[b], n = m + r;
+    if (m == 0) continue;
+    double rows = r, cols = r;
+    for (int o = 0; o < ipow(3, d); ++o) {
+      int oo = o;
+      for (int k = 0; k < d; ++k) {
+        q[k] = bc[k] + (oo % 3) - 1;
+        oo /= 3;
+      }
+      if (!in_grid(q, d, F.n) || cheb(bc, q, d) == 0) continue;
+      int qb = morton_key(q, d, l);
+      double sz = colour_of(q, d) < cb ? F.h_r[qb] : F.h_m[qb];
+      rows += sz;
+      cols += sz;
+    }
+    fl += 2.0 / 3.0 * n * n * n + 2.0 * n * n * cols + 2.0 * (rows - r) * m * cols;
+  }
+  return fl;
+}
+
+int run_factor(Handle& h) {
+  const int L = h.L;
+  cudaStream_t st = h.stream;
+  h.fac.assign(L + 1, FacLevel());
+  h.max_rank_factor = 0;
+  h.flops_factor = 0;
+  for (int l = L; l >= 2; --l) {
+    int e = setup_level(h, l);
+    if (e) return e;
+    e = factor_level(h, l);
+    if (e) return e;
+    h.flops_factor += level_flops(h, l);
+  }
+  // top: dense level-1 system in the level-2 multipoles
+  FacLevel& F2 = h.fac[2];
+  h.top_off.assign(F2.nb + 1, 0);
+  for (int b = 0; b < F2.nb; ++b) h.top_off[b + 1] = h.top_off[b] + F2.h_r[b];
+  h.ntop = h.top_off[F2.nb];
+  const int nt = std::max(1, h.ntop);
+  h.top = hnew<double>(h, (size_t)nt * nt);
+  h.top_ipiv = hnew<int>(h, nt);
+  int* toff = hnew<int>(h, F2.nb + 1, false);
+  double* cm = hnew<double>(h, nt);
+  LuItem* it = hnew<LuItem>(h, 1, false);
+  if (!h.top || !h.top_ipiv || !toff || !cm || !it) return HOOM;
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * (F2.nb + 1), cudaMemcpyHostToDevice, st));
+  LV v2 = view(h, F2);
+  k_top_assemble<<<dim3(F2.nb, F2.ns6), 256, 0, st>>>(v2, toff, h.top, h.ntop);
+  LuItem hi;
+  hi.a = h.top;
+  hi.ipiv = h.top_ipiv;
+  hi.colmax = cm;
+  hi.n = h.ntop;
+  hi.ld = h.ntop;
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(it, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
+  k_colmax<<<1, 256, 0, st>>>(it, cm, nt);
+  for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
+    k_lu_panel<<<1, 256, 0, st>>>(it, k0, h.derr);
+    k_lu_trsm<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0);
+    int tiles = (h.ntop + 63) / 64;
+    k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0);
+  }
+  h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));
+  int er = check_derr(h);
+  if (er) {
+    h.err = "top-level LU: singular";
+    return HSINGULAR;
+  }
+  return HOK;
+}
+
+}  // namespace aifmm

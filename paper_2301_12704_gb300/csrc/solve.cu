@@ -1,0 +1,537 @@
+// Solve phase on the GPU (Sec. 3.6, Algorithm 3 and the Remark after it):
+// the right-hand-side Schur operations replayed in elimination order
+// (forward sweep, part of T_As), the dense level-1 solve for the level-2
+// multipoles, and back substitution level 2..L in reverse colour order.
+// Also the NNCA H^2 product (upward P2M/M2M, M2L, downward L2L/L2P, P2P) and
+// the exact direct-sum product used to measure true residuals.
+#include <algorithm>
+
+#include "dense.cuh"
+#include "internal.h"
+#include "level.cuh"
+
+namespace aifmm {
+
+namespace {
+
+LV view(Handle& h, FacLevel& F) {
+  LV v;
+  v.l = F.l;
+  v.d = h.d;
+  v.n = F.n;
+  v.nb = F.nb;
+  v.M = F.M;
+  v.R = F.R;
+  v.P = F.P;
+  v.Rp = F.Rp;
+  v.ns5 = F.ns5;
+  v.ns6 = F.ns6;
+  v.m = F.m;
+  v.r = F.r;
+  v.XX = F.XX;
+  v.XY = F.XY;
+  v.LX = F.LX;
+  v.LY = F.LY;
+  v.U = F.U;
+  v.V = F.V;
+  v.Ud = F.Ud;
+  v.Vd = F.Vd;
+  v.LU = F.LU;
+  v.ipiv = F.ipiv;
+  v.flag = F.flag;
+  return v;
+}
+
+// per-level solve vectors: X rows (m), Lc rows (r), solution x (m); each box
+// holds an (M x nrhs) / (R x nrhs) column-major block.
+struct SV {
+  double* bX;
+  double* bL;
+  double* xX;
+  double* w;      // per-box workspace (P x nrhs)
+  int nrhs;
+};
+
+__device__ inline double* bx(const LV& v, const SV& s, int b) { return s.bX + (size_t)b * v.M * s.nrhs; }
+__device__ inline double* bl(const LV& v, const SV& s, int b) { return s.bL + (size_t)b * v.R * s.nrhs; }
+__device__ inline double* xx_(const LV& v, const SV& s, int b) { return s.xX + (size_t)b * v.M * s.nrhs; }
+__device__ inline double* ws(const LV& v, const SV& s, int b) { return s.w + (size_t)b * v.P * s.nrhs; }
+
+// original-order rhs -> leaf X rows (tree order)
+__global__ void k_leaf_in(LV v, SV s, const int* __restrict__ start, const int* __restrict__ perm,
+                          const double* __restrict__ rhs, int64_t ld) {
+  int b = blockIdx.x;
+  int st = start[b], m = start[b + 1] - st;
+  for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
+    int i = e % m, k = e / m;
+    bx(v, s, b)[i + (size_t)k * v.M] = rhs[perm[st + i] + (size_t)k * ld];
+  }
+}
+
+__global__ void k_leaf_out(LV v, SV s, const int* __restrict__ start, const int* __restrict__ perm,
+                           double* __restrict__ x, int64_t ld) {
+  int b = blockIdx.x;
+  int st = start[b], m = start[b + 1] - st;
+  for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
+    int i = e % m, k = e / m;
+    x[perm[st + i] + (size_t)k * ld] = xx_(v, s, b)[i + (size_t)k * v.M];
+  }
+}
+
+// in-block LU solve of an n x n factor (ld lda) on X (n x nrhs, ld ldx)
+__device__ void block_lu_solve(const double* A, int lda, const int* ipiv, int n, double* X, int ldx, int nrhs) {
+  if (threadIdx.x < nrhs)
+    for (int k = 0; k < n; ++k) {
+      int p = ipiv[k];
+      if (p != k) {
+        double t = X[k + (size_t)threadIdx.x * ldx];
+        X[k + (size_t)threadIdx.x * ldx] = X[p + (size_t)threadIdx.x * ldx];
+        X[p + (size_t)threadIdx.x * ldx] = t;
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    for (int e = threadIdx.x; e < (n - k - 1) * nrhs; e += blockDim.x) {
+      int i = k + 1 + e % (n - k - 1), c = e / (n - k - 1);
+      X[i + (size_t)c * ldx] -= A[i + (size_t)k * lda] * X[k + (size_t)c * ldx];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (threadIdx.x < nrhs) X[k + (size_t)threadIdx.x * ldx] /= A[k + (size_t)k * lda];
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
+      int i = e % k, c = e / k;
+      X[i + (size_t)c * ldx] -= A[i + (size_t)k * lda] * X[k + (size_t)c * ldx];
+    }
+    __syncthreads();
+  }
+}
+
+// forward sweep, step 1: w = Piv^-1 [beta; 0] for each box of the colour
+__global__ void __launch_bounds__(256) k_fwd_lu(LV v, SV s, int col) {
+  int b = colour_box(col, blockIdx.x, v.d, v.l);
+  const int m = v.m[b], r = v.r[b], n = m + r;
+  if (m == 0) return;
+  double* w = ws(v, s, b);
+  const double* beta = bx(v, s, b);
+  for (int e = threadIdx.x; e < n * s.nrhs; e += blockDim.x) {
+    int i = e % n, k = e / n;
+    w[i + (size_t)k * v.P] = i < m ? beta[i + (size_t)k * v.M] : 0.0;
+  }
+  __syncthreads();
+  block_lu_solve(v.lu(b), v.P, v.piv(b), n, w, v.P, s.nrhs);
+}
+
+// forward sweep, step 2: right-hand-side Schur operations on the coupled
+// rows: X_p -= K_pb w_x (p not yet eliminated), Lc_p -= P2L_pb w_x
+// (p eliminated), Lc_b += w_z.  grid (3^d, cnt)
+__global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col) {
+  int b = colour_box(col, blockIdx.y, v.d, v.l);
+  const int m = v.m[b], r = v.r[b];
+  if (m == 0) return;
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  int oo = blockIdx.x;
+  for (int k = 0; k < 3; ++k) q[k] = bc[k];
+  for (int k = 0; k < v.d; ++k) {
+    q[k] = bc[k] + (oo % 3) - 1;
+    oo /= 3;
+  }
+  if (!in_grid(q, v.d, v.n)) return;
+  int p = morton_key(q, v.d, v.l);
+  const double* w = ws(v, s, b);
+  if (p == b) {
+    double* t = bl(v, s, b);
+    for (int e = threadIdx.x; e < r * s.nrhs; e += blockDim.x) {
+      int i = e % r, k = e / r;
+      t[i + (size_t)k * v.R] += w[m + i + (size_t)k * v.P];
+    }
+    return;
+  }
+  bool elim = colour_of(q, v.d) < col;
+  int sp = slot5(q, bc, v.d);
+  const double* A;
+  int lda, rows;
+  double* t;
+  int ldt;
+  if (elim) {
+    A = v.lx(p, sp);
+    lda = v.R;
+    rows = v.r[p];
+    t = bl(v, s, p);
+    ldt = v.R;
+  } else {
+    A = v.xx(p, sp);
+    lda = v.M;
+    rows = v.m[p];
+    t = bx(v, s, p);
+    ldt = v.M;
+  }
+  for (int e = threadIdx.x; e < rows * s.nrhs; e += blockDim.x) {
+    int i = e % rows, k = e / rows;
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) acc += A[i + (size_t)j * lda] * w[j + (size_t)k * v.P];
+    t[i + (size_t)k * ldt] -= acc;
+  }
+}
+
+// level transition of the right-hand side: X rows of parent P are the Lc
+// rows of its children
+__global__ void k_rhs_up(LV vc, SV sc, LV vp, SV sp, const int* __restrict__ cxoff) {
+  int P = blockIdx.x;
+  int nch = 1 << vc.d;
+  for (int a = 0; a < nch; ++a) {
+    int c = (P << vc.d) + a;
+    int r = vc.r[c], o = cxoff[c];
+    const double* src = bl(vc, sc, c);
+    double* dst = bx(vp, sp, P);
+    for (int e = threadIdx.x; e < r * sc.nrhs; e += blockDim.x) {
+      int i = e % r, k = e / r;
+      dst[o + i + (size_t)k * vp.M] = src[i + (size_t)k * vc.R];
+    }
+  }
+}
+
+__global__ void k_top_in(LV v, SV s, const int* __restrict__ toff, double* __restrict__ y, int ntop) {
+  int b = blockIdx.x;
+  int r = v.r[b], o = toff[b];
+  for (int e = threadIdx.x; e < r * s.nrhs; e += blockDim.x) {
+    int i = e % r, k = e / r;
+    y[o + i + (size_t)k * ntop] = bl(v, s, b)[i + (size_t)k * v.R];
+  }
+}
+
+// multipoles y_q of level l: from the level-1 solution (l = 2) or from the
+// parent's particles (l >= 3)
+struct YSrc {
+  const double* top;
+  int ntop;
+  const int* toff;
+  const double* px;    // parent level x
+  int pM;
+  const int* xoff;
+  int d;
+};
+
+__device__ inline double yval(const YSrc& y, int l, int q, int i, int k, int nrhs) {
+  if (l == 2) return y.top[y.toff[q] + i + (size_t)k * y.ntop];
+  int P = q >> y.d;
+  return y.px[(size_t)P * y.pM * nrhs + y.xoff[q] + i + (size_t)k * y.pM];
+}
+
+// back substitution for the boxes of a colour: [x_b; z_b] = Piv^-1
+// [beta_b - sum K_bq x_q - sum M2P_br y_r ; y_b]
+__global__ void __launch_bounds__(256) k_bwd(LV v, SV s, int col, YSrc y) {
+  int b = colour_box(col, blockIdx.x, v.d, v.l);
+  const int m = v.m[b], r = v.r[b], n = m + r;
+  if (m == 0) return;
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  double* w = ws(v, s, b);
+  const double* beta = bx(v, s, b);
+  for (int e = threadIdx.x; e < n * s.nrhs; e += blockDim.x) {
+    int i = e % n, k = e / n;
+    w[i + (size_t)k * v.P] = i < m ? beta[i + (size_t)k * v.M] : yval(y, v.l, b, i - m, k, s.nrhs);
+  }
+  __syncthreads();
+  int n3 = ipow(3, v.d);
+  for (int o = 0; o < n3; ++o) {
+    int oo = o;
+    for (int k = 0; k < 3; ++k) q[k] = bc[k];
+    for (int k = 0; k < v.d; ++k) {
+      q[k] = bc[k] + (oo % 3) - 1;
+      oo /= 3;
+    }
+    if (!in_grid(q, v.d, v.n)) continue;
+    int p = morton_key(q, v.d, v.l);
+    if (p == b) continue;
+    int sq = slot5(bc, q, v.d);
+    bool elim = colour_of(q, v.d) < col;
+    int cols = elim ? v.r[p] : v.m[p];
+    const double* A = elim ? v.xy(b, sq) : v.xx(b, sq);
+    for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
+      int i = e % m, k = e / m;
+      double acc = 0.0;
+      if (elim)
+        for (int j = 0; j < cols; ++j) acc += A[i + (size_t)j * v.M] * yval(y, v.l, p, j, k, s.nrhs);
+      else
+        for (int j = 0; j < cols; ++j) acc += A[i + (size_t)j * v.M] * xx_(v, s, p)[j + (size_t)k * v.M];
+      w[i + (size_t)k * v.P] -= acc;
+    }
+    __syncthreads();
+  }
+  block_lu_solve(v.lu(b), v.P, v.piv(b), n, w, v.P, s.nrhs);
+  double* xo = xx_(v, s, b);
+  for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
+    int i = e % m, k = e / m;
+    xo[i + (size_t)k * v.M] = w[i + (size_t)k * v.P];
+  }
+}
+
+__global__ void k_top_solve(const double* A, const int* ipiv, int n, double* X, int nrhs) {
+  block_lu_solve(A, n, ipiv, n, X, n, nrhs);
+}
+
+// ---------------------------------------------------------------- H^2 product
+// upward: q_b = U_b^T x_b (leaf) or U_b^T [q_children] ; one block per box
+__global__ void k_h2_up(const int* __restrict__ m, const int* __restrict__ rank, const double* __restrict__ U,
+                        int M, int R, const double* __restrict__ xin, int ldin, const int* __restrict__ inoff,
+                        double* __restrict__ qout, int nrhs, int d, int leaf, const int* __restrict__ start,
+                        const int* __restrict__ crank) {
+  int b = blockIdx.x;
+  int mb = m[b], rb = rank[b];
+  const double* Ub = U + (size_t)b * M * R;
+  for (int e = threadIdx.x; e < rb * nrhs; e += blockDim.x) {
+    int j = e % rb, k = e / rb;
+    double acc = 0.0;
+    if (leaf) {
+      int s0 = start[b];
+      for (int i = 0; i < mb; ++i) acc += Ub[i + (size_t)j * M] * xin[s0 + i + (size_t)k * ldin];
+    } else {
+      // children multipoles, stacked in child order (rank R_c slots each)
+      int i = 0;
+      for (int c = b << d; c < (b + 1) << d; ++c) {
+        int rc = crank[c];
+        for (int a = 0; a < rc; ++a, ++i) acc += Ub[i + (size_t)j * M] * xin[(size_t)c * ldin * nrhs + a + (size_t)k * ldin];
+      }
+    }
+    qout[(size_t)b * R * nrhs + j + (size_t)k * R] = acc;
+  }
+}
+
+// M2L: z_b = sum_{d in IL(b)} A(t^{b,i}, t^{d,i}) q_d ; one block per box
+__global__ void k_h2_m2l(int l, int d, const int* __restrict__ rank, const int* __restrict__ piv, int R,
+                         const double* __restrict__ q, double* __restrict__ z, int nrhs, KParams kp, Pts P) {
+  int b = blockIdx.x;
+  int n = 1 << l;
+  int bc[3], qc[3];
+  morton_coords(b, d, l, bc);
+  int rb = rank[b];
+  int ns6 = ipow(6, d);
+  for (int e = threadIdx.x; e < rb * nrhs; e += blockDim.x) {
+    int i = e % rb, k = e / rb;
+    double acc = 0.0;
+    for (int s = 0; s < ns6; ++s) {
+      slot6_coords(bc, s, d, qc);
+      if (!in_grid(qc, d, n) || cheb(bc, qc, d) <= 1) continue;
+      int db = morton_key(qc, d, l);
+      int rd = rank[db];
+      for (int j = 0; j < rd; ++j)
+        acc += keval(kp, P, piv[(size_t)b * R + i], piv[(size_t)db * R + j]) * q[(size_t)db * R * nrhs + j + (size_t)k * R];
+    }
+    z[(size_t)b * R * nrhs + i + (size_t)k * R] = acc;
+  }
+}
+
+// downward: z_c += U^dag_c z_P = U_P[rows of c] z_P ; one block per child
+__global__ void k_h2_down(int d, const int* __restrict__ crank, int cR, double* __restrict__ zc,
+                          const int* __restrict__ prank, const double* __restrict__ pU, int pM, int pR,
+                          const double* __restrict__ zp, int nrhs) {
+  int c = blockIdx.x;
+  int P = c >> d;
+  int off = 0;
+  for (int s = P << d; s < c; ++s) off += crank[s];
+  int rc = crank[c], rp = prank[P];
+  const double* UP = pU + (size_t)P * pM * pR;
+  for (int e = threadIdx.x; e < rc * nrhs; e += blockDim.x) {
+    int i = e % rc, k = e / rc;
+    double acc = 0.0;
+    for (int j = 0; j < rp; ++j) acc += UP[off + i + (size_t)j * pM] * zp[(size_t)P * pR * nrhs + j + (size_t)k * pR];
+    zc[(size_t)c * cR * nrhs + i + (size_t)k * cR] += acc;
+  }
+}
+
+// leaf: y_b = U_b z_b + sum_{q in N(b)} K_bq x_q (tree order vectors)
+__global__ void k_h2_leaf(int L, int d, const int* __restrict__ start, const int* __restrict__ rank,
+                          const double* __restrict__ U, int M, int R, const double* __restrict__ z,
+                          const double* __restrict__ x, double* __restrict__ y, int N, int nrhs, KParams kp, Pts P) {
+  int b = blockIdx.x;
+  int n = 1 << L;
+  int bc[3], qc[3];
+  morton_coords(b, d, L, bc);
+  int s0 = start[b], mb = start[b + 1] - s0, rb = rank[b];
+  const double* Ub = U + (size_t)b * M * R;
+  int n3 = ipow(3, d);
+  for (int e = threadIdx.x; e < mb * nrhs; e += blockDim.x) {
+    int i = e % mb, k = e / mb;
+    double acc = 0.0;
+    for (int j = 0; j < rb; ++j) acc += Ub[i + (size_t)j * M] * z[(size_t)b * R * nrhs + j + (size_t)k * R];
+    for (int o = 0; o < n3; ++o) {
+      int oo = o;
+      for (int kk = 0; kk < 3; ++kk) qc[kk] = bc[kk];
+      for (int kk = 0; kk < d; ++kk) {
+        qc[kk] = bc[kk] + (oo % 3) - 1;
+        oo /= 3;
+      }
+      if (!in_grid(qc, d, n)) continue;
+      int qb = morton_key(qc, d, L);
+      int t0 = start[qb], t1 = start[qb + 1];
+      for (int j = t0; j < t1; ++j) acc += keval(kp, P, s0 + i, j) * x[j + (size_t)k * N];
+    }
+    y[s0 + i + (size_t)k * N] = acc;
+  }
+}
+
+__global__ void k_permute_in(const int* __restrict__ perm, int N, const double* __restrict__ src, int64_t ld,
+                             double* __restrict__ dst, int nrhs) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * nrhs; e += gridDim.x * blockDim.x) {
+    int t = e % N, k = e / N;
+    dst[t + (size_t)k * N] = src[perm[t] + (size_t)k * ld];
+  }
+}
+
+__global__ void k_permute_out(const int* __restrict__ perm, int N, const double* __restrict__ src,
+                              double* __restrict__ dst, int64_t ld, int nrhs) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * nrhs; e += gridDim.x * blockDim.x) {
+    int t = e % N, k = e / N;
+    dst[perm[t] + (size_t)k * ld] = src[t + (size_t)k * N];
+  }
+}
+
+// exact direct sum y = A x in tree order; one thread per row, points staged
+// through shared memory
+__global__ void __launch_bounds__(256) k_direct(const double* __restrict__ x, double* __restrict__ y, int N, int nrhs,
+                                                KParams kp, Pts P) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  double acc = 0.0;
+  for (int j = 0; j < N; ++j)
+    if (i < N) acc += keval(kp, P, i, j) * x[j + (size_t)k * N];
+  if (i < N) y[i + (size_t)k * N] = acc;
+}
+
+}  // namespace
+
+int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
+  const int L = h.L, d = h.d;
+  cudaStream_t st = h.stream;
+  std::vector<SV> sv(L + 1);
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    size_t nb = F.nb;
+    sv[l].nrhs = nrhs;
+    sv[l].bX = (double*)hscratch(h, 100 + 4 * l, sizeof(double) * nb * F.M * nrhs);
+    sv[l].bL = (double*)hscratch(h, 101 + 4 * l, sizeof(double) * nb * F.R * nrhs);
+    sv[l].xX = (double*)hscratch(h, 102 + 4 * l, sizeof(double) * nb * F.M * nrhs);
+    sv[l].w = (double*)hscratch(h, 103 + 4 * l, sizeof(double) * nb * F.P * nrhs);
+    if (!sv[l].bX || !sv[l].bL || !sv[l].xX || !sv[l].w) return HOOM;
+    AIFMM_CUDA_TRY(h, cudaMemsetAsync(sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
+  }
+  const int ncol = ipow(3, d);
+  // ---- forward sweep
+  {
+    LV v = view(h, h.fac[L]);
+    k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld);
+  }
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    LV v = view(h, F);
+    for (int col = 0; col < ncol; ++col) {
+      int cnt = colour_count(col, d, F.n);
+      if (!cnt) continue;
+      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col);
+      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col);
+    }
+    if (l > 2) {
+      FacLevel& Fp = h.fac[l - 1];
+      LV vp = view(h, Fp);
+      k_rhs_up<<<Fp.nb, 256, 0, st>>>(v, sv[l], vp, sv[l - 1], F.xoff);
+    }
+  }
+  // ---- top
+  const int nt = std::max(1, h.ntop);
+  double* ytop = (double*)hscratch(h, 99, sizeof(double) * (size_t)nt * nrhs);
+  int* toff = (int*)hscratch(h, 98, sizeof(int) * (h.top_off.size()));
+  if (!ytop || !toff) return HOOM;
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice, st));
+  {
+    LV v2 = view(h, h.fac[2]);
+    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop);
+    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs);
+  }
+  // ---- back substitution, levels 2..L, colours in reverse
+  for (int l = 2; l <= L; ++l) {
+    FacLevel& F = h.fac[l];
+    LV v = view(h, F);
+    YSrc y;
+    y.top = ytop;
+    y.ntop = h.ntop;
+    y.toff = toff;
+    y.d = d;
+    if (l > 2) {
+      y.px = sv[l - 1].xX;
+      y.pM = h.fac[l - 1].M;
+      y.xoff = F.xoff;
+    } else {
+      y.px = nullptr;
+      y.pM = 0;
+      y.xoff = F.xoff;
+    }
+    for (int col = ncol - 1; col >= 0; --col) {
+      int cnt = colour_count(col, d, F.n);
+      if (!cnt) continue;
+      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y);
+    }
+  }
+  {
+    LV v = view(h, h.fac[L]);
+    k_leaf_out<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld);
+  }
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  return HOK;
+}
+
+int run_h2_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t ld) {
+  const int L = h.L, d = h.d, N = (int)h.N;
+  cudaStream_t st = h.stream;
+  double* xt = (double*)hscratch(h, 200, sizeof(double) * (size_t)N * nrhs);
+  double* yt = (double*)hscratch(h, 201, sizeof(double) * (size_t)N * nrhs);
+  if (!xt || !yt) return HOOM;
+  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs);
+  std::vector<double*> q(L + 1), z(L + 1);
+  for (int l = 2; l <= L; ++l) {
+    NnLevel& Nl = h.nn[l];
+    q[l] = (double*)hscratch(h, 202 + 2 * l, sizeof(double) * (size_t)Nl.nb * Nl.R * nrhs);
+    z[l] = (double*)hscratch(h, 203 + 2 * l, sizeof(double) * (size_t)Nl.nb * Nl.R * nrhs);
+    if (!q[l] || !z[l]) return HOOM;
+  }
+  for (int l = L; l >= 2; --l) {
+    NnLevel& Nl = h.nn[l];
+    if (l == L)
+      k_h2_up<<<Nl.nb, 128, 0, st>>>(Nl.m, Nl.rank, Nl.U, Nl.M, Nl.R, xt, N, nullptr, q[l], nrhs, d, 1,
+                                     h.start + h.soff[L], nullptr);
+    else
+      k_h2_up<<<Nl.nb, 128, 0, st>>>(Nl.m, Nl.rank, Nl.U, Nl.M, Nl.R, q[l + 1], h.nn[l + 1].R, nullptr, q[l], nrhs,
+                                     d, 0, nullptr, h.nn[l + 1].rank);
+  }
+  for (int l = 2; l <= L; ++l) {
+    NnLevel& Nl = h.nn[l];
+    k_h2_m2l<<<Nl.nb, 128, 0, st>>>(l, d, Nl.rank, Nl.pivpos, Nl.R, q[l], z[l], nrhs, h.kp, h.P());
+    if (l > 2) {
+      NnLevel& Np = h.nn[l - 1];
+      k_h2_down<<<Nl.nb, 128, 0, st>>>(d, Nl.rank, Nl.R, z[l], Np.rank, Np.U, Np.M, Np.R, z[l - 1], nrhs);
+    }
+  }
+  NnLevel& NL = h.nn[L];
+  k_h2_leaf<<<NL.nb, 128, 0, st>>>(L, d, h.start + h.soff[L], NL.rank, NL.U, NL.M, NL.R, z[L], xt, yt, N, nrhs,
+                                   h.kp, h.P());
+  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs);
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  return HOK;
+}
+
+int run_direct_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t ld) {
+  const int N = (int)h.N;
+  cudaStream_t st = h.stream;
+  double* xt = (double*)hscratch(h, 200, sizeof(double) * (size_t)N * nrhs);
+  double* yt = (double*)hscratch(h, 201, sizeof(double) * (size_t)N * nrhs);
+  if (!xt || !yt) return HOOM;
+  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs);
+  k_direct<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(xt, yt, N, nrhs, h.kp, h.P());
+  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs);
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  return HOK;
+}
+
+}  // namespace aifmm
