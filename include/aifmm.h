@@ -73,6 +73,8 @@ typedef struct {
   int order;       /* 0: distance-2 colour order (default), only value supported */
   int depth;       /* 0: depth from the average-occupancy rule; >= 2: force depth L */
   void* stream;    /* cudaStream_t to run on; NULL = the library's own stream */
+  int profile;     /* 1: time the factorisation's kernel groups with CUDA events
+                      on the handle's stream (reported by aifmm_stats) */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of
@@ -89,6 +91,13 @@ typedef struct {
   double bytes_solve;       /* algorithmic bytes streamed by one solve sweep pair, nrhs=1 */
   double bytes_resident;    /* device bytes held by the handle */
   double ms_build, ms_factor, ms_solve, ms_matvec;
+  int64_t kernel_launches;  /* kernels launched by the handle so far */
+  /* profile mode: CUDA-event time, algorithmic FP64 flops and launches of the
+     factorisation's kernel groups, summed over the last aifmm_factor:
+     [0] compress and redirect, [1] pivot LU, [2] Z = Piv^-1 B, [3] Schur update */
+  double group_ms[4];
+  double group_flops[4];
+  int64_t group_launches[4];
 } aifmm_stats_t;
 
 /* Build the tree, interaction lists, NNCA operators and extended system.

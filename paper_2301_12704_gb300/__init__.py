@@ -38,7 +38,7 @@ class Kernel(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p)]
+    _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("max_rank_factor", C.c_int), ("max_m", C.c_int), ("top_size", C.c_int),
                 ("flops_factor", C.c_double), ("bytes_solve", C.c_double), ("bytes_resident", C.c_double),
                 ("ms_build", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
-                ("ms_matvec", C.c_double)]
+                ("ms_matvec", C.c_double), ("kernel_launches", C.c_int64), ("group_ms", C.c_double * 4),
+                ("group_flops", C.c_double * 4), ("group_launches", C.c_int64 * 4)]
 
 
 _lib = None
@@ -109,13 +110,13 @@ class Handle:
 
 
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
-                depth: int = 0, stream=None) -> Handle:
+                depth: int = 0, stream=None, profile: bool = False) -> Handle:
     """Build tree, lists, NNCA operators and the extended system (C: aifmm_build)."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
-    o = Options(0, int(depth), C.c_void_p(stream) if stream else None)
+    o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)))
     out = C.c_void_p()
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
@@ -173,7 +174,11 @@ def aifmm_direct_matvec(h: Handle, x):
 def aifmm_stats(h: Handle) -> dict:
     s = Stats()
     _check(lib().aifmm_stats(h.raw, C.byref(s)), h.raw)
-    return {f: getattr(s, f) for f, _ in Stats._fields_}
+    out = {}
+    for f, _ in Stats._fields_:
+        v = getattr(s, f)
+        out[f] = list(v) if hasattr(v, "__len__") else v
+    return out
 
 
 def aifmm_levels(h: Handle) -> int:

@@ -157,6 +157,7 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.kp.dim = k->dim;
   h.kp.diag = k->diag;
   h.kp.inv_len2 = k->kind == AIFMM_K_GAUSS ? 1.0 / (k->length * k->length) : 0.0;
+  h.profile = opt && opt->profile;
   if (opt && opt->stream) {
     h.stream = (cudaStream_t)opt->stream;
   } else {
@@ -351,6 +352,12 @@ aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {
   o->ms_factor = h.ms_factor;
   o->ms_solve = h.ms_solve;
   o->ms_matvec = h.ms_matvec;
+  o->kernel_launches = h.nlaunch;
+  for (int g = 0; g < 4; ++g) {
+    o->group_ms[g] = h.g_ms[g];
+    o->group_flops[g] = h.g_flops[g];
+    o->group_launches[g] = h.g_launch[g];
+  }
   return AIFMM_OK;
 }
 

@@ -1013,20 +1013,52 @@ static int setup_level(Handle& h, int l) {
   LV v = view(h, F);
   const int n3 = ipow(3, d);
   if (l == L) {
-    k_setup_leaf_K<<<dim3(F.nb, n3), 256, 0, st>>>(v, h.start + h.soff[L], h.kp, h.P());
-    k_copy_basis<<<F.nb, 256, 0, st>>>(v, N.U, N.M, N.R);
+    k_setup_leaf_K<<<dim3(F.nb, n3), 256, 0, st>>>(v, h.start + h.soff[L], h.kp, h.P()); ++h.nlaunch;
+    k_copy_basis<<<F.nb, 256, 0, st>>>(v, N.U, N.M, N.R); ++h.nlaunch;
   } else {
     FacLevel& C = h.fac[l + 1];
     LV vc = view(h, C);
-    k_setup_parent<<<dim3(F.nb, n3), 256, 0, st>>>(v, vc, C.xoff);
+    k_setup_parent<<<dim3(F.nb, n3), 256, 0, st>>>(v, vc, C.xoff); ++h.nlaunch;
   }
-  k_setup_m2l<<<dim3(F.nb, F.ns6), 128, 0, st>>>(v, N.pivpos, N.R, h.kp, h.P());
+  k_setup_m2l<<<dim3(F.nb, F.ns6), 128, 0, st>>>(v, N.pivpos, N.R, h.kp, h.P()); ++h.nlaunch;
   if (l >= 3) {
     const NnLevel& Np = h.nn[l - 1];
-    k_setup_udag<<<F.nb, 128, 0, st>>>(v, Np.U, Np.M, Np.R, Np.rank, N.rank);
+    k_setup_udag<<<F.nb, 128, 0, st>>>(v, Np.U, Np.M, Np.R, Np.rank, N.rank); ++h.nlaunch;
   }
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   return HOK;
+}
+
+// profile mode: bracket a group of launches with CUDA events on the stream
+struct GroupTimer {
+  Handle& h;
+  int g;
+  cudaEvent_t a = nullptr, b = nullptr;
+  long long n0;
+  GroupTimer(Handle& hh, int gg) : h(hh), g(gg), n0(hh.nlaunch) {
+    if (!h.profile) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h.stream);
+  }
+  ~GroupTimer() {
+    if (!h.profile) return;
+    cudaEventRecord(b, h.stream);
+    h.g_ev.push_back({g, {a, b}});
+    h.g_launch[g] += h.nlaunch - n0;
+  }
+};
+
+static void collect_group_times(Handle& h) {
+  for (auto& e : h.g_ev) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.second.second);
+    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+    h.g_ms[e.first] += ms;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  h.g_ev.clear();
 }
 
 static int factor_level(Handle& h, int l) {
@@ -1057,17 +1089,19 @@ static int factor_level(Handle& h, int l) {
     c.rn = ib + 4 * cnt;
     c.rold = ib + 5 * cnt;
     c.skip = ib + 6 * cnt;
-    k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c);
-    k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c);
-    k_cmp_qrcp<<<dim3(cnt, 2), 512, 0, st>>>(v, c);
-    k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c);
-    k_cmp_lmat<<<dim3(cnt, 2), 256, 0, st>>>(v, c);
-    k_cmp_row_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c);
-    k_cmp_row_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c);
-    k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c);
-    k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c);
-    k_cmp_col_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c);
-    k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c);
+    GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
+    k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_qrcp<<<dim3(cnt, 2), 512, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_lmat<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_row_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_row_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_col_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    delete gt;
     // ---- pivot LU
     Elim e;
     e.col = col;
@@ -1084,20 +1118,26 @@ static int factor_level(Handle& h, int l) {
     e.nrow = eb;
     e.ncol = eb + cnt;
     e.totc = eb + 2 * cnt;
-    k_coupled<<<(cnt + 127) / 128, 128, 0, st>>>(v, e);
-    k_piv_build<<<cnt, 256, 0, st>>>(v, e);
-    k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P);
+    k_coupled<<<(cnt + 127) / 128, 128, 0, st>>>(v, e); ++h.nlaunch;
+    gt = new GroupTimer(h, Handle::G_PIVLU);
+    k_piv_build<<<cnt, 256, 0, st>>>(v, e); ++h.nlaunch;
+    k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P); ++h.nlaunch;
     for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
-      k_lu_panel<<<cnt, 256, 0, st>>>(e.lu, k0, h.derr);
-      k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0);
+      k_lu_panel<<<cnt, 256, 0, st>>>(e.lu, k0, h.derr); ++h.nlaunch;
+      k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
       int tiles = (F.P + 63) / 64;
-      k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+      k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
     }
+    delete gt;
     // ---- Z = Piv^-1 B and the Schur update
-    k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e);
-    k_lu_solve_strip<<<dim3((e.ncmax + 31) / 32, cnt), 256, 0, st>>>(e.sv);
+    gt = new GroupTimer(h, Handle::G_ZSOLVE);
+    k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e); ++h.nlaunch;
+    k_lu_solve_strip<<<dim3((e.ncmax + 31) / 32, cnt), 256, 0, st>>>(e.sv); ++h.nlaunch;
+    delete gt;
     int tpb = (F.M + 63) / 64;
-    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb);
+    gt = new GroupTimer(h, Handle::G_SCHUR);
+    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb); ++h.nlaunch;
+    delete gt;
     AIFMM_CUDA_TRY(h, cudaGetLastError());
   }
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(F.h_r.data(), F.r, sizeof(int) * F.nb, cudaMemcpyDeviceToHost, st));
@@ -1108,7 +1148,7 @@ static int factor_level(Handle& h, int l) {
             (er == DERR_SINGULAR ? ": singular pivot block" : " (device error " + std::to_string(er) + ")");
     return er == DERR_SINGULAR ? HSINGULAR : HCAPACITY;
   }
-  k_xoff<<<(F.nb + 127) / 128, 128, 0, st>>>(F.nb, d, F.r, F.xoff);
+  k_xoff<<<(F.nb + 127) / 128, 128, 0, st>>>(F.nb, d, F.r, F.xoff); ++h.nlaunch;
   for (int b = 0; b < F.nb; ++b) h.max_rank_factor = std::max(h.max_rank_factor, F.h_r[b]);
   return HOK;
 }
@@ -1139,7 +1179,11 @@ static double level_flops(Handle& h, int l) {
       rows += sz;
       cols += sz;
     }
-    fl += 2.0 / 3.0 * n * n * n + 2.0 * n * n * cols + 2.0 * (rows - r) * m * cols;
+    double flu = 2.0 / 3.0 * n * n * n, fz = 2.0 * n * n * cols, fs = 2.0 * (rows - r) * m * cols;
+    h.g_flops[Handle::G_PIVLU] += flu;
+    h.g_flops[Handle::G_ZSOLVE] += fz;
+    h.g_flops[Handle::G_SCHUR] += fs;
+    fl += flu + fz + fs;
   }
   return fl;
 }
@@ -1150,11 +1194,13 @@ int run_factor(Handle& h) {
   h.fac.assign(L + 1, FacLevel());
   h.max_rank_factor = 0;
   h.flops_factor = 0;
+  for (int g = 0; g < Handle::G_NG; ++g) h.g_ms[g] = h.g_flops[g] = 0, h.g_launch[g] = 0;
   for (int l = L; l >= 2; --l) {
     int e = setup_level(h, l);
     if (e) return e;
     e = factor_level(h, l);
     if (e) return e;
+    collect_group_times(h);
     h.flops_factor += level_flops(h, l);
   }
   // top: dense level-1 system in the level-2 multipoles
@@ -1171,7 +1217,7 @@ int run_factor(Handle& h) {
   if (!h.top || !h.top_ipiv || !toff || !cm || !it) return HOOM;
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * (F2.nb + 1), cudaMemcpyHostToDevice, st));
   LV v2 = view(h, F2);
-  k_top_assemble<<<dim3(F2.nb, F2.ns6), 256, 0, st>>>(v2, toff, h.top, h.ntop);
+  k_top_assemble<<<dim3(F2.nb, F2.ns6), 256, 0, st>>>(v2, toff, h.top, h.ntop); ++h.nlaunch;
   LuItem hi;
   hi.a = h.top;
   hi.ipiv = h.top_ipiv;
@@ -1179,12 +1225,12 @@ int run_factor(Handle& h) {
   hi.n = h.ntop;
   hi.ld = h.ntop;
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(it, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
-  k_colmax<<<1, 256, 0, st>>>(it, cm, nt);
+  k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
-    k_lu_panel<<<1, 256, 0, st>>>(it, k0, h.derr);
-    k_lu_trsm<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0);
+    k_lu_panel<<<1, 256, 0, st>>>(it, k0, h.derr); ++h.nlaunch;
+    k_lu_trsm<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
-    k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0);
+    k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
   }
   h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;
   AIFMM_CUDA_TRY(h, cudaGetLastError());

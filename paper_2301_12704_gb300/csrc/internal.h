@@ -88,6 +88,14 @@ struct Handle {
   double ms_build = 0, ms_factor = 0, ms_solve = 0, ms_matvec = 0;
   double flops_factor = 0;
   int max_rank_nnca = 0, max_rank_factor = 0, max_m = 0;
+  // launch count and optional per-kernel-group event timing (profile mode)
+  long long nlaunch = 0;
+  bool profile = false;
+  enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_NG = 4 };
+  double g_ms[G_NG] = {0, 0, 0, 0};
+  double g_flops[G_NG] = {0, 0, 0, 0};
+  long long g_launch[G_NG] = {0, 0, 0, 0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> g_ev;
   Pts P() const {
     Pts p;
     p.x = pts;

@@ -508,17 +508,17 @@ int build_nnca(Handle& h) {
     N.U = hnew<double>(h, (size_t)nb * M * R);
     if (!N.m || !N.rank || !N.rows || !N.pivloc || !N.pivpos || !N.far || !N.U) return HOOM;
     if (l == L) {
-      k_leaf_rows<<<nb, 128, 0, st>>>(startl, nb, M, N.m, N.rows);
+      k_leaf_rows<<<nb, 128, 0, st>>>(startl, nb, M, N.m, N.rows); ++h.nlaunch;
     } else {
       const NnLevel& C = h.nn[l + 1];
-      k_parent_rows<<<nb, 128, 0, st>>>(d, nb, C.rank, C.pivpos, C.R, M, N.m, N.rows);
+      k_parent_rows<<<nb, 128, 0, st>>>(d, nb, C.rank, C.pivpos, C.R, M, N.m, N.rows); ++h.nlaunch;
     }
     // interaction-list tables
     int* ils = (int*)hscratch(h, 0, sizeof(int) * (size_t)nb * ilmax);
     int* ilo = (int*)hscratch(h, 1, sizeof(int) * (size_t)nb * (ilmax + 1));
     int* nil = (int*)hscratch(h, 2, sizeof(int) * (size_t)nb);
     if (!ils || !ilo || !nil) return HOOM;
-    k_il_table<<<(nb + 127) / 128, 128, 0, st>>>(l, d, startl, ilmax, ils, ilo, nil);
+    k_il_table<<<(nb + 127) / 128, 128, 0, st>>>(l, d, startl, ilmax, ils, ilo, nil); ++h.nlaunch;
     // ACA workspace
     const int nchunk = (F + CHUNK - 1) / CHUNK;
     AcaArgs a;
@@ -556,18 +556,18 @@ int build_nnca(Handle& h) {
     a.eps = h.tol;
     a.kp = h.kp;
     a.P = h.P();
-    k_aca_init<<<(nb + 127) / 128, 128, 0, st>>>(a);
+    k_aca_init<<<(nb + 127) / 128, 128, 0, st>>>(a); ++h.nlaunch;
     dim3 gchunk(nchunk, nb);
     int iters = 0;
     const int maxit = M + 2;
     while (iters < maxit) {
       for (int q = 0; q < 8 && iters < maxit; ++q, ++iters) {
-        k_aca_row<<<gchunk, 256, 0, st>>>(a);
-        k_aca_col<<<nb, 256, 0, st>>>(a);
-        k_aca_scale<<<gchunk, 256, 0, st>>>(a);
-        k_aca_commit<<<nb, 32, 0, st>>>(a);
+        k_aca_row<<<gchunk, 256, 0, st>>>(a); ++h.nlaunch;
+        k_aca_col<<<nb, 256, 0, st>>>(a); ++h.nlaunch;
+        k_aca_scale<<<gchunk, 256, 0, st>>>(a); ++h.nlaunch;
+        k_aca_commit<<<nb, 32, 0, st>>>(a); ++h.nlaunch;
       }
-      k_count_active<<<1, 32, 0, st>>>(a.st, nb, active);
+      k_count_active<<<1, 32, 0, st>>>(a.st, nb, active); ++h.nlaunch;
       int hact = 0;
       AIFMM_CUDA_TRY(h, cudaMemcpyAsync(&hact, active, sizeof(int), cudaMemcpyDeviceToHost, st));
       AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));
@@ -578,7 +578,7 @@ int build_nnca(Handle& h) {
     int* ip_ws = (int*)hscratch(h, 13, sizeof(int) * (size_t)nb * R);
     if (!lu_ws || !ip_ws) return HOOM;
     k_nnca_U<<<nb, 256, 0, st>>>(M, R, N.m, N.rank, N.rows, N.pivpos, N.far, lu_ws, ip_ws, N.U, h.kp, h.P(),
-                                 h.derr);
+                                 h.derr); ++h.nlaunch;
     AIFMM_CUDA_TRY(h, cudaGetLastError());
     N.h_rank.assign(nb, 0);
     AIFMM_CUDA_TRY(h, cudaMemcpyAsync(N.h_rank.data(), N.rank, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));

@@ -422,7 +422,7 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
   // ---- forward sweep
   {
     LV v = view(h, h.fac[L]);
-    k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld);
+    k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
   }
   for (int l = L; l >= 2; --l) {
     FacLevel& F = h.fac[l];
@@ -430,13 +430,13 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
     for (int col = 0; col < ncol; ++col) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
-      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col);
-      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col);
+      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
+      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
     }
     if (l > 2) {
       FacLevel& Fp = h.fac[l - 1];
       LV vp = view(h, Fp);
-      k_rhs_up<<<Fp.nb, 256, 0, st>>>(v, sv[l], vp, sv[l - 1], F.xoff);
+      k_rhs_up<<<Fp.nb, 256, 0, st>>>(v, sv[l], vp, sv[l - 1], F.xoff); ++h.nlaunch;
     }
   }
   // ---- top
@@ -447,8 +447,8 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice, st));
   {
     LV v2 = view(h, h.fac[2]);
-    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop);
-    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs);
+    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop); ++h.nlaunch;
+    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs); ++h.nlaunch;
   }
   // ---- back substitution, levels 2..L, colours in reverse
   for (int l = 2; l <= L; ++l) {
@@ -471,12 +471,12 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
     for (int col = ncol - 1; col >= 0; --col) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
-      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y);
+      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
     }
   }
   {
     LV v = view(h, h.fac[L]);
-    k_leaf_out<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld);
+    k_leaf_out<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
   }
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   return HOK;
@@ -488,7 +488,7 @@ int run_h2_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t ld) {
   double* xt = (double*)hscratch(h, 200, sizeof(double) * (size_t)N * nrhs);
   double* yt = (double*)hscratch(h, 201, sizeof(double) * (size_t)N * nrhs);
   if (!xt || !yt) return HOOM;
-  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs);
+  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs); ++h.nlaunch;
   std::vector<double*> q(L + 1), z(L + 1);
   for (int l = 2; l <= L; ++l) {
     NnLevel& Nl = h.nn[l];
@@ -498,25 +498,26 @@ int run_h2_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t ld) {
   }
   for (int l = L; l >= 2; --l) {
     NnLevel& Nl = h.nn[l];
-    if (l == L)
+    if (l == L) {
       k_h2_up<<<Nl.nb, 128, 0, st>>>(Nl.m, Nl.rank, Nl.U, Nl.M, Nl.R, xt, N, nullptr, q[l], nrhs, d, 1,
-                                     h.start + h.soff[L], nullptr);
-    else
+                                     h.start + h.soff[L], nullptr); ++h.nlaunch;
+    } else {
       k_h2_up<<<Nl.nb, 128, 0, st>>>(Nl.m, Nl.rank, Nl.U, Nl.M, Nl.R, q[l + 1], h.nn[l + 1].R, nullptr, q[l], nrhs,
-                                     d, 0, nullptr, h.nn[l + 1].rank);
+                                     d, 0, nullptr, h.nn[l + 1].rank); ++h.nlaunch;
+    }
   }
   for (int l = 2; l <= L; ++l) {
     NnLevel& Nl = h.nn[l];
-    k_h2_m2l<<<Nl.nb, 128, 0, st>>>(l, d, Nl.rank, Nl.pivpos, Nl.R, q[l], z[l], nrhs, h.kp, h.P());
+    k_h2_m2l<<<Nl.nb, 128, 0, st>>>(l, d, Nl.rank, Nl.pivpos, Nl.R, q[l], z[l], nrhs, h.kp, h.P()); ++h.nlaunch;
     if (l > 2) {
       NnLevel& Np = h.nn[l - 1];
-      k_h2_down<<<Nl.nb, 128, 0, st>>>(d, Nl.rank, Nl.R, z[l], Np.rank, Np.U, Np.M, Np.R, z[l - 1], nrhs);
+      k_h2_down<<<Nl.nb, 128, 0, st>>>(d, Nl.rank, Nl.R, z[l], Np.rank, Np.U, Np.M, Np.R, z[l - 1], nrhs); ++h.nlaunch;
     }
   }
   NnLevel& NL = h.nn[L];
   k_h2_leaf<<<NL.nb, 128, 0, st>>>(L, d, h.start + h.soff[L], NL.rank, NL.U, NL.M, NL.R, z[L], xt, yt, N, nrhs,
-                                   h.kp, h.P());
-  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs);
+                                   h.kp, h.P()); ++h.nlaunch;
+  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs); ++h.nlaunch;
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   return HOK;
 }
@@ -527,9 +528,9 @@ int run_direct_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t l
   double* xt = (double*)hscratch(h, 200, sizeof(double) * (size_t)N * nrhs);
   double* yt = (double*)hscratch(h, 201, sizeof(double) * (size_t)N * nrhs);
   if (!xt || !yt) return HOOM;
-  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs);
-  k_direct<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(xt, yt, N, nrhs, h.kp, h.P());
-  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs);
+  k_permute_in<<<512, 256, 0, st>>>(h.perm, N, x, ld, xt, nrhs); ++h.nlaunch;
+  k_direct<<<dim3((N + 255) / 256, nrhs), 256, 0, st>>>(xt, yt, N, nrhs, h.kp, h.P()); ++h.nlaunch;
+  k_permute_out<<<512, 256, 0, st>>>(h.perm, N, yt, y, ld, nrhs); ++h.nlaunch;
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   return HOK;
 }

@@ -173,12 +173,12 @@ int build_tree(Handle& h, const double* aos) {
   if (!soa || !soa2 || !key || !count || !fill || !tmp || !h.perm || !h.bbox || !h.start) return HOOM;
   int grid = (N + 255) / 256;
   if (grid > 4096) grid = 4096;
-  k_aos_to_soa<<<grid, 256, 0, st>>>(aos, N, d, soa);
-  k_bbox<<<1, 1024, 0, st>>>(soa, N, d, h.bbox);
-  k_leaf_keys<<<grid, 256, 0, st>>>(soa, N, d, L, h.bbox, key, count);
+  k_aos_to_soa<<<grid, 256, 0, st>>>(aos, N, d, soa); ++h.nlaunch;
+  k_bbox<<<1, 1024, 0, st>>>(soa, N, d, h.bbox); ++h.nlaunch;
+  k_leaf_keys<<<grid, 256, 0, st>>>(soa, N, d, L, h.bbox, key, count); ++h.nlaunch;
   int* leaf_start = h.start + h.soff[L];
-  k_scan<<<1, 1024, 0, st>>>(count, nleaf, leaf_start);
-  k_scatter<<<grid, 256, 0, st>>>(key, N, leaf_start, fill, tmp);
+  k_scan<<<1, 1024, 0, st>>>(count, nleaf, leaf_start); ++h.nlaunch;
+  k_scatter<<<grid, 256, 0, st>>>(key, N, leaf_start, fill, tmp); ++h.nlaunch;
   // leaf occupancy bound for the shared-memory rank sort
   h.h_leaf_start.resize(nleaf + 1);
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(h.h_leaf_start.data(), leaf_start, sizeof(int) * (nleaf + 1),
@@ -192,13 +192,13 @@ int build_tree(Handle& h, const double* aos) {
             " (use a deeper tree)";
     return HCAPACITY;
   }
-  k_sort_segments<<<nleaf, 256, sizeof(int) * (occ > 0 ? occ : 1), st>>>(leaf_start, tmp, h.perm, cap, h.derr);
-  k_gather_points<<<grid, 256, 0, st>>>(soa, h.perm, N, d, soa2);
-  k_check_duplicates<<<nleaf, 128, 0, st>>>(soa2, N, d, leaf_start, h.derr);
+  k_sort_segments<<<nleaf, 256, sizeof(int) * (occ > 0 ? occ : 1), st>>>(leaf_start, tmp, h.perm, cap, h.derr); ++h.nlaunch;
+  k_gather_points<<<grid, 256, 0, st>>>(soa, h.perm, N, d, soa2); ++h.nlaunch;
+  k_check_duplicates<<<nleaf, 128, 0, st>>>(soa2, N, d, leaf_start, h.derr); ++h.nlaunch;
   h.pts = soa2;
   for (int l = 0; l < L; ++l) {
     int nb = 1 << (d * l);
-    k_level_starts<<<(nb + 256) / 256, 256, 0, st>>>(leaf_start, d * (L - l), nb, h.start + h.soff[l]);
+    k_level_starts<<<(nb + 256) / 256, 256, 0, st>>>(leaf_start, d * (L - l), nb, h.start + h.soff[l]); ++h.nlaunch;
   }
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));
