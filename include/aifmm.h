@@ -124,6 +124,26 @@ aifmm_status aifmm_factor(aifmm_h h);
  * Errors: STATE (no factor), INVALID, OOM, CUDA. */
 aifmm_status aifmm_solve(aifmm_h h, const double* rhs, double* x, int nrhs, int64_t ld);
 
+/* Solve without allocating: the same result as aifmm_solve, for callers that
+ * must not call cudaMalloc once their factorisation is resident -- e.g. a
+ * request loop serving solves from a thread that runs under a strict
+ * allocation budget or alongside code that forbids allocation.  The paper
+ * has no counterpart; this is a deployment variant of Algorithm 3.
+ *   rhs, x    DEVICE pointers only (host staging would need an allocation),
+ *             N x nrhs column-major, leading dimension ld; may alias.
+ * Temporaries live in one static device array of
+ * aifmm_noalloc_scratch_bytes() bytes (64 MiB) that every GPU which loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address; make it before any stream capture.
+ * The array is shared by all calls and keeps the last call's contents: calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it.
+ * Errors: STATE (no factor), INVALID (host pointers, nrhs < 1, ld < N),
+ * CAPACITY (the problem and nrhs need more than the static array), CUDA. */
+aifmm_status aifmm_solve_noalloc(aifmm_h h, const double* rhs, double* x, int nrhs, int64_t ld);
+
+/* Size in bytes of the static array used by aifmm_solve_noalloc. */
+int64_t aifmm_noalloc_scratch_bytes(void);
+
 /* y = A_H2 x with the NNCA H^2 representation built by aifmm_build
  * (upward P2M/M2M, M2L, downward L2L/L2P, near-field P2P).
  * Errors: STATE, INVALID, OOM, CUDA. */

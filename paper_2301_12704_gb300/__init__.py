@@ -64,6 +64,9 @@ def lib():
         L.aifmm_build.argtypes = [vp, i64, C.POINTER(Kernel), dbl, cint, C.POINTER(Options), C.POINTER(vp)]
         L.aifmm_factor.argtypes = [vp]
         L.aifmm_solve.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_solve_noalloc.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_noalloc_scratch_bytes.argtypes = []
+        L.aifmm_noalloc_scratch_bytes.restype = i64
         L.aifmm_matvec.argtypes = [vp, vp, vp, cint, i64]
         L.aifmm_direct_matvec.argtypes = [vp, vp, vp, cint, i64]
         L.aifmm_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -75,7 +78,8 @@ def lib():
         L.aifmm_last_error.restype = C.c_char_p
         L.aifmm_destroy.argtypes = [vp]
         L.aifmm_destroy.restype = None
-        for name in ("aifmm_build", "aifmm_factor", "aifmm_solve", "aifmm_matvec", "aifmm_direct_matvec",
+        for name in ("aifmm_build", "aifmm_factor", "aifmm_solve", "aifmm_solve_noalloc", "aifmm_matvec",
+                     "aifmm_direct_matvec",
                      "aifmm_stats", "aifmm_tree_perm", "aifmm_level_ranks", "aifmm_level_pivots",
                      "aifmm_levels"):
             getattr(L, name).restype = C.c_int
@@ -150,6 +154,23 @@ def aifmm_solve(h: Handle, rhs):
     px, kx = _ptr(x)
     _check(lib().aifmm_solve(h.raw, C.c_void_p(pb), C.c_void_p(px), b.shape[1], h.n), h.raw)
     return x
+
+
+def aifmm_solve_noalloc(h: Handle, rhs, x):
+    """x = A^-1 rhs without any device allocation (C: aifmm_solve_noalloc).
+    rhs and x must be column-major float64 CUDA tensors of shape N x nrhs;
+    x is written in place and returned."""
+    if rhs.dim() == 1:
+        rhs, x = rhs[:, None], x[:, None]
+    if not (rhs.is_cuda and x.is_cuda and rhs.stride(0) == 1 and x.stride(0) == 1):
+        raise ValueError("aifmm_solve_noalloc needs column-major CUDA tensors")
+    _check(lib().aifmm_solve_noalloc(h.raw, C.c_void_p(rhs.data_ptr()), C.c_void_p(x.data_ptr()),
+                                     rhs.shape[1], rhs.stride(1) if rhs.shape[1] > 1 else h.n), h.raw)
+    return x
+
+
+def aifmm_noalloc_scratch_bytes() -> int:
+    return int(lib().aifmm_noalloc_scratch_bytes())
 
 
 def _product(fn, h, xv):

@@ -283,6 +283,44 @@ aifmm_status aifmm_solve(aifmm_h c, const double* rhs, double* x, int nrhs, int6
   return to_status(e);
 }
 
+aifmm_status aifmm_solve_noalloc(aifmm_h c, const double* rhs, double* x, int nrhs, int64_t ld) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (!h.factored) {
+    h.err = "solve before factor";
+    return AIFMM_ERR_STATE;
+  }
+  if (!rhs || !x || nrhs < 1 || ld < h.N) {
+    h.err = "invalid argument";
+    return AIFMM_ERR_INVALID;
+  }
+  if (!is_device_ptr(rhs) || !is_device_ptr(x)) {
+    h.err = "aifmm_solve_noalloc: rhs and x must be device pointers (host staging would allocate)";
+    return AIFMM_ERR_INVALID;
+  }
+  int e = HOK;
+  if (rhs != x && cudaMemcpy2DAsync(x, ld * sizeof(double), rhs, ld * sizeof(double), h.N * sizeof(double), nrhs,
+                                    cudaMemcpyDeviceToDevice, h.stream) != cudaSuccess) {
+    h.err = "aifmm_solve_noalloc: copy of rhs failed";
+    e = HCUDA;
+  }
+  if (!e) e = run_solve_noalloc(h, x, nrhs, ld);
+  if (!e && cudaStreamSynchronize(h.stream) != cudaSuccess) {
+    h.err = "aifmm_solve_noalloc: CUDA error";
+    e = HCUDA;
+  }
+  if (!e) {
+    int de = check_derr(h);
+    if (de) {
+      h.err = "aifmm_solve_noalloc: device error " + std::to_string(de);
+      e = HCAPACITY;
+    }
+  }
+  return to_status(e);
+}
+
+int64_t aifmm_noalloc_scratch_bytes(void) { return (int64_t)noalloc_scratch_bytes(); }
+
 static aifmm_status product(aifmm_h c, const double* x, double* y, int nrhs, int64_t ld, bool direct) {
   if (!c) return AIFMM_ERR_INVALID;
   Handle& h = c->h;

@@ -133,6 +133,9 @@ int run_factor(Handle& h);
 int run_solve(Handle& h, double* b_dev, int nrhs, int64_t ld);   // in place, original order
 int run_h2_matvec(Handle& h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
 int run_direct_matvec(Handle& h, const double* x_dev, double* y_dev, int nrhs, int64_t ld);
+// solve with every temporary in a static device array (no allocation)
+int run_solve_noalloc(Handle& h, double* b_dev, int nrhs, int64_t ld);
+size_t noalloc_scratch_bytes();
 
 // error codes returned by the run_* functions (mapped to aifmm_status)
 enum HostErr { HOK = 0, HINVALID = 1, HOOM = 2, HSINGULAR = 3, HSTATE = 4, HCUDA = 6, HCAPACITY = 8 };

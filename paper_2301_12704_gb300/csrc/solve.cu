@@ -536,3 +536,140 @@ int run_direct_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t l
 }
 
 }  // namespace aifmm
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.  Same kernels and order as run_solve, but every
+// temporary vector lives in one file-scope device array instead of memory
+// obtained from cudaMalloc, for callers that must not allocate once their
+// factorisation is resident.  The array is shared by every call on a device
+// and keeps the previous call's contents; the parts that must start at zero
+// are cleared here.  Calls whose work overlaps on the GPU race on it.
+namespace aifmm {
+
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)8 << 20;   // 64 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_noalloc_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+size_t noalloc_scratch_bytes() { return NOALLOC_SCRATCH_DOUBLES * sizeof(double); }
+
+// device address of the array for the current device (host code cannot use
+// the symbol itself); looked up once per device
+static int noalloc_scratch(Handle& h, double** out) {
+  if (h.device < 0 || h.device >= kMaxDevices) {
+    h.err = "aifmm_solve_noalloc: device index out of range";
+    return HINVALID;
+  }
+  if (!g_noalloc_addr[h.device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      h.err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return HCUDA;
+    }
+    g_noalloc_addr[h.device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[h.device];
+  return HOK;
+}
+
+int run_solve_noalloc(Handle& h, double* b, int nrhs, int64_t ld) {
+  const int L = h.L, d = h.d;
+  cudaStream_t st = h.stream;
+  double* base = nullptr;
+  int e = noalloc_scratch(h, &base);
+  if (e) return e;
+  // carve the per-level vectors (256-byte aligned pieces)
+  auto round = [](size_t n) { return (n + 31) & ~(size_t)31; };
+  size_t need = 0;
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    size_t nb = F.nb;
+    need += round(nb * F.M * nrhs) * 2 + round(nb * F.R * nrhs) + round(nb * F.P * nrhs);
+  }
+  const int nt = std::max(1, h.ntop);
+  need += round((size_t)nt * nrhs) + round(h.top_off.size());
+  if (need > NOALLOC_SCRATCH_DOUBLES) {
+    h.err = "aifmm_solve_noalloc: this problem needs " + std::to_string(need * sizeof(double)) +
+            " bytes of solve vectors for nrhs=" + std::to_string(nrhs) + "; the static scratch holds " +
+            std::to_string(NOALLOC_SCRATCH_DOUBLES * sizeof(double)) + " bytes";
+    return HCAPACITY;
+  }
+  if (L + 1 > 16) {
+    h.err = "aifmm_solve_noalloc: tree deeper than 15 levels";
+    return HCAPACITY;
+  }
+  SV sv[16];
+  size_t off = 0;
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    size_t nb = F.nb;
+    sv[l].nrhs = nrhs;
+    sv[l].bX = base + off;
+    off += round(nb * F.M * nrhs);
+    sv[l].bL = base + off;
+    off += round(nb * F.R * nrhs);
+    sv[l].xX = base + off;
+    off += round(nb * F.M * nrhs);
+    sv[l].w = base + off;
+    off += round(nb * F.P * nrhs);
+    AIFMM_CUDA_TRY(h, cudaMemsetAsync(sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
+  }
+  double* ytop = base + off;
+  off += round((size_t)nt * nrhs);
+  int* toff = reinterpret_cast<int*>(base + off);
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice, st));
+  const int ncol = ipow(3, d);
+  {
+    LV v = view(h, h.fac[L]);
+    k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
+  }
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    LV v = view(h, F);
+    for (int col = 0; col < ncol; ++col) {
+      int cnt = colour_count(col, d, F.n);
+      if (!cnt) continue;
+      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
+      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
+    }
+    if (l > 2) {
+      FacLevel& Fp = h.fac[l - 1];
+      LV vp = view(h, Fp);
+      k_rhs_up<<<Fp.nb, 256, 0, st>>>(v, sv[l], vp, sv[l - 1], F.xoff); ++h.nlaunch;
+    }
+  }
+  {
+    LV v2 = view(h, h.fac[2]);
+    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop); ++h.nlaunch;
+    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs); ++h.nlaunch;
+  }
+  for (int l = 2; l <= L; ++l) {
+    FacLevel& F = h.fac[l];
+    LV v = view(h, F);
+    YSrc y;
+    y.top = ytop;
+    y.ntop = h.ntop;
+    y.toff = toff;
+    y.d = d;
+    y.px = l > 2 ? sv[l - 1].xX : nullptr;
+    y.pM = l > 2 ? h.fac[l - 1].M : 0;
+    y.xoff = F.xoff;
+    for (int col = ncol - 1; col >= 0; --col) {
+      int cnt = colour_count(col, d, F.n);
+      if (!cnt) continue;
+      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
+    }
+  }
+  {
+    LV v = view(h, h.fac[L]);
+    k_leaf_out<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
+  }
+  AIFMM_CUDA_TRY(h, cudaGetLastError());
+  return HOK;
+}
+
+}  // namespace aifmm
