@@ -264,6 +264,8 @@ def main():
            "residual_direct_sum": resid, "flops_factor": stats0["flops_factor"],
            "factor_fp64_tflops": stats0["flops_factor"] / (tf / args.steps / 1e3) / 1e12,
            "group_ms_per_factor": {n: groups_ms[i] / args.steps for i, n in enumerate(names)},
+           "group_tflops": {n: (groups_fl[i] / (groups_ms[i] / 1e3) / 1e12 if groups_ms[i] > 0 else 0.0)
+                            for i, n in enumerate(names)},
            "roofline": roof, "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall}
 
     if not args.no_e2e:

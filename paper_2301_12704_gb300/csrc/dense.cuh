@@ -201,3 +201,133 @@ static __global__ void k_colmax(const LuItem* items, double* out, int stride) {
 }
 
 }  // namespace aifmm
+
+namespace aifmm {
+
+// ---- blocked multi-RHS LU solve:  X := U^-1 L^-1 P X  -------------------------
+// Row interchanges of every right-hand-side column (one thread per column).
+static __global__ void __launch_bounds__(128) k_lus_swap(const SolveItem* items) {
+  SolveItem it = items[blockIdx.y];
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= it.ncols || it.n == 0) return;
+  double* X = it.x + (size_t)c * it.ldx;
+  for (int k = 0; k < it.n; ++k) {
+    int p = it.ipiv[k];
+    if (p != k) {
+      double t = X[k];
+      X[k] = X[p];
+      X[p] = t;
+    }
+  }
+}
+
+constexpr int TB = 64;   // diagonal block of the blocked triangular solves
+
+// diagonal block k0..k0+TB of the unit-lower (lower=1) or upper (lower=0)
+// factor applied to every column; the block sits in shared memory, one
+// thread per column keeps its TB entries in registers.
+template <int LOWER>
+static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items, int k0) {
+  __shared__ double T[TB][TB + 1];
+  SolveItem it = items[blockIdx.y];
+  int n = it.n;
+  if (k0 >= n) return;
+  int nb = min(TB, n - k0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e % TB, j = e / TB;
+    T[i][j] = (i < nb && j < nb) ? it.a[(k0 + i) + (size_t)(k0 + j) * it.ld] : 0.0;
+  }
+  __syncthreads();
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= it.ncols) return;
+  double* X = it.x + (size_t)c * it.ldx + k0;
+  double x[TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i) x[i] = i < nb ? X[i] : 0.0;
+  if (LOWER) {
+#pragma unroll
+    for (int j = 0; j < TB; ++j)
+#pragma unroll
+      for (int i = j + 1; i < TB; ++i) x[i] -= T[i][j] * x[j];
+  } else {
+#pragma unroll
+    for (int j = TB - 1; j >= 0; --j) {
+      if (j < nb) x[j] /= T[j][j];
+#pragma unroll
+      for (int i = 0; i < j; ++i) x[i] -= T[i][j] * x[j];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TB; ++i)
+    if (i < nb) X[i] = x[i];
+}
+
+// trailing update after diagonal block k0: lower -> rows below, upper -> rows
+// above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)
+template <int LOWER>
+static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* items, int k0) {
+  SolveItem it = items[blockIdx.z];
+  int n = it.n;
+  if (k0 >= n) return;
+  int nb = min(TB, n - k0);
+  int r0, r1;
+  if (LOWER) {
+    r0 = k0 + nb;
+    r1 = n;
+  } else {
+    r0 = 0;
+    r1 = k0;
+  }
+  int i0 = r0 + blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= r1 || j0 >= it.ncols) return;
+  tile_gemm_64(it.a + i0 + (size_t)k0 * it.ld, it.ld, it.x + k0 + (size_t)j0 * it.ldx, it.ldx,
+               it.x + i0 + (size_t)j0 * it.ldx, it.ldx, r1 - i0, it.ncols - j0, nb, -1.0);
+}
+
+}  // namespace aifmm
+
+namespace aifmm {
+
+// 64x64 FP64 tile with a transposed left operand:
+// C[0..mr, 0..nc] += alpha * A^T B, A column-major K x mr (lda), B K x nc (ldb)
+__device__ inline void tile_gemm_64_tn(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                       int mr, int nc, int K, double alpha) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int k2 = e & 15, ii = e >> 4;
+      As[k2][ii] = (ii < mr && k0 + k2 < K) ? A[(k0 + k2) + (size_t)ii * lda] : 0.0;
+      Bs[k2][ii] = (ii < nc && k0 + k2 < K) ? B[(k0 + k2) + (size_t)ii * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc[a][b];
+    }
+}
+
+}  // namespace aifmm

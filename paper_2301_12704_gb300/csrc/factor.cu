@@ -23,6 +23,8 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <cooperative_groups.h>
+
 #include "dense.cuh"
 #include "internal.h"
 #include "level.cuh"
@@ -202,6 +204,8 @@ struct Cmp {
   int* skip;           // [cnt] 1 if nothing is pending
   double* Lm;          // [cnt][2][R*R] L_b (side 0), R_b (side 1), ld R
   double eps;
+  double* flops;       // device accumulator of algorithmic flops (compress group)
+  int* err;
 };
 
 // fill-in flags are read with a load that bypasses the non-coherent cache
@@ -310,12 +314,25 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 // Householder QR with column pivoting; the first nf = r_b columns are taken
 // in order, then the largest residual column among the fill-ins while its
 // norm exceeds eps * max_j ||F_j||.  Produces Q[:, :rank] explicitly.
-// grid (cnt, 2), 512 threads.
-__global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
+// One thread-block cluster of QC CTAs per (box, side): CTA c updates the
+// trailing columns j with j % QC == c; the pivot is reduced across the
+// cluster through distributed shared memory; CTA 0 swaps columns and builds
+// each reflector.  Every CTA derives the loop exit from the same cluster-wide
+// values, so all of them pass the same sequence of cluster barriers.
+// grid (QC * 2 * cnt), 256 threads.
+constexpr int QC = 8;
+
+__global__ void __cluster_dims__(QC, 1, 1) __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   __shared__ double shv[32];
   __shared__ int shi[32];
   __shared__ double shs[32];
-  int t = blockIdx.x, side = blockIdx.y;
+  __shared__ ArgMax lbest;
+  __shared__ double lmax;
+  const int cr = (int)cl.block_rank();
+  const int bs = blockIdx.x / QC;
+  const int t = bs >> 1, side = bs & 1;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   const int m = v.m[b], n = c.nc[t * 2 + side], nf = c.rold[t];
@@ -324,28 +341,27 @@ __global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
   double* cn = c.cn + ((size_t)t * 2 + side) * c.WC;
   double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // initial column norms and the threshold
+  // initial column norms of the fill-in columns and the threshold
   double mx = 0.0;
-  for (int j = nf + w; j < n; j += nw) {
+  for (int j = nf + cr + QC * w; j < n; j += QC * nw) {
     double acc = 0.0;
     for (int i = lane; i < m; i += 32) acc += W[i + (size_t)j * M] * W[i + (size_t)j * M];
     acc = warp_sum(acc);
     if (lane == 0) cn[j] = acc;
     mx = fmax(mx, acc);
   }
-  // block max of mx
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __syncthreads();
   if (lane == 0) shs[w] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
     for (int q = 0; q < nw; ++q) a = fmax(a, shs[q]);
-    shs[0] = a;
+    lmax = a;
   }
-  __syncthreads();
-  const double tau = c.eps * sqrt(shs[0]);
-  __syncthreads();
+  cl.sync();
+  double gmax = 0.0;
+  for (int r = 0; r < QC; ++r) gmax = fmax(gmax, *cl.map_shared_rank(&lmax, r));
+  const double tau = c.eps * sqrt(gmax);
   const int kmax = min(m, n);
   int k = 0;
   for (; k < kmax; ++k) {
@@ -353,16 +369,23 @@ __global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
       ArgMax best;
       best.v = -1.0;
       best.i = -1;
-      for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
+      int j0 = k + ((cr - k % QC) + QC) % QC;   // first j >= k with j % QC == cr
+      for (int j = j0 + QC * threadIdx.x; j < n; j += QC * blockDim.x) {
         ArgMax x;
         x.v = cn[j];
         x.i = j;
         best = amax_pick(best, x);
       }
       best = block_amax(best, shv, shi);
-      if (!(sqrt(fmax(best.v, 0.0)) > tau)) break;
-      int p = best.i;
-      if (p != k) {
+      if (threadIdx.x == 0) lbest = best;
+      cl.sync();
+      ArgMax g;
+      g.v = -1.0;
+      g.i = -1;
+      for (int r = 0; r < QC; ++r) g = amax_pick(g, *cl.map_shared_rank(&lbest, r));
+      if (!(sqrt(fmax(g.v, 0.0)) > tau)) break;
+      if (cr == 0 && g.i != k) {
+        int p = g.i;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
           double x = W[i + (size_t)k * M];
           W[i + (size_t)k * M] = W[i + (size_t)p * M];
@@ -373,31 +396,32 @@ __global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
           cn[k] = cn[p];
           cn[p] = x;
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
-    // reflector from W[k:m, k]
-    double acc = 0.0;
-    for (int i = k + threadIdx.x; i < m; i += blockDim.x) acc += W[i + (size_t)k * M] * W[i + (size_t)k * M];
-    double a2 = block_sum(acc, shs);
-    double alpha = sqrt(a2);
-    double x0 = W[k + (size_t)k * M];
-    __syncthreads();
-    if (alpha == 0.0) {
-      // identity reflector: mark with a zero vector
-      for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] = 0.0;
+    if (cr == 0) {
+      // reflector from W[k:m, k], stored normalised in place
+      double acc = 0.0;
+      for (int i = k + threadIdx.x; i < m; i += blockDim.x) acc += W[i + (size_t)k * M] * W[i + (size_t)k * M];
+      double a2 = block_sum(acc, shs);
+      double alpha = sqrt(a2);
+      double x0 = W[k + (size_t)k * M];
       __syncthreads();
-      continue;
+      if (alpha == 0.0) {
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] = 0.0;
+      } else {
+        double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
+        double nv = sqrt(a2 - x0 * x0 + v0 * v0);
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+          double x = i == k ? v0 : W[i + (size_t)k * M];
+          W[i + (size_t)k * M] = x / nv;
+        }
+      }
     }
-    double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
-    // ||v||^2 = a2 - x0^2 + v0^2
-    double nv = sqrt(a2 - x0 * x0 + v0 * v0);
-    if (threadIdx.x == 0) W[k + (size_t)k * M] = v0;
-    __syncthreads();
-    for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] /= nv;
-    __syncthreads();
-    // apply to the trailing columns and refresh their residual norms
-    for (int j = k + 1 + w; j < n; j += nw) {
+    cl.sync();
+    // apply H_k to the trailing columns owned by this CTA, refresh norms
+    int j0 = (k + 1) + ((cr - (k + 1) % QC) + QC) % QC;
+    for (int j = j0 + QC * w; j < n; j += QC * nw) {
       double dt = 0.0;
       for (int i = k + lane; i < m; i += 32) dt += W[i + (size_t)k * M] * W[i + (size_t)j * M];
       dt = warp_sum(dt);
@@ -410,15 +434,16 @@ __global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
       nn = warp_sum(nn);
       if (lane == 0) cn[j] = nn;
     }
-    __syncthreads();
+    cl.sync();
   }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
   const int rank = k;
   // form Q[:, :rank] = H_0 ... H_{rank-1} [e_0 .. e_{rank-1}]
-  for (int j = w; j < rank; j += nw) {
+  for (int j = cr + QC * w; j < rank; j += QC * nw) {
     double* y = Q + (size_t)j * M;
     for (int i = lane; i < m; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
     __syncwarp();
-    for (int kk = rank - 1; kk >= 0; --kk) {
+    for (int kk = min(j, rank - 1); kk >= 0; --kk) {
       double dt = 0.0;
       for (int i = kk + lane; i < m; i += 32) dt += W[i + (size_t)kk * M] * y[i];
       dt = warp_sum(dt);
@@ -426,14 +451,20 @@ __global__ void __launch_bounds__(512) k_cmp_qrcp(LV v, Cmp c) {
       __syncwarp();
     }
   }
-  if (threadIdx.x == 0) c.rk[t * 2 + side] = rank;
+  if (cr == 0 && threadIdx.x == 0) {
+    c.rk[t * 2 + side] = rank;
+    double f = 2.0 * m * (n - nf);
+    for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
+    atomicAdd(c.flops, f);
+  }
 }
 
-// equal ranks: the smaller side takes the other side's extra basis columns,
-// orthogonalised against its own by a Householder QR with every column forced.
-// grid cnt, 256 threads.  Uses the side's W workspace as scratch.
+// equal ranks: the smaller side takes the other side's extra basis columns
+// k..rn-1, orthogonalised against its own k columns (classical Gram-Schmidt
+// applied twice) and then among themselves.  grid cnt, 256 threads.
 __global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
   __shared__ double shs[32];
+  __shared__ double proj[1024];
   int t = blockIdx.x;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -446,71 +477,63 @@ __global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
     if (k >= rn) continue;
     double* Qs = c.Q + ((size_t)t * 2 + side) * M * M;
     const double* Qo = c.Q + ((size_t)t * 2 + (1 - side)) * M * M;
-    double* A = c.W + ((size_t)t * 2 + side) * M * c.WC;   // m x rn
-    for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
-      int i = e % m, j = e / m;
-      A[i + (size_t)j * M] = j < k ? Qs[i + (size_t)j * M] : Qo[i + (size_t)j * M];
-    }
-    __syncthreads();
-    for (int kk = 0; kk < rn; ++kk) {
-      double acc = 0.0;
-      for (int i = kk + threadIdx.x; i < m; i += blockDim.x) acc += A[i + (size_t)kk * M] * A[i + (size_t)kk * M];
-      double a2 = block_sum(acc, shs);
-      double alpha = sqrt(a2);
-      double x0 = A[kk + (size_t)kk * M];
+    for (int j = k; j < rn; ++j) {
+      double* x = Qs + (size_t)j * M;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] = Qo[i + (size_t)j * M];
       __syncthreads();
-      if (alpha == 0.0) {
-        for (int i = kk + threadIdx.x; i < m; i += blockDim.x) A[i + (size_t)kk * M] = 0.0;
+      double n0 = sqrt(block_sum([&] {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) a += x[i] * x[i];
+        return a;
+      }(), shs));
+      for (int pass = 0; pass < 2; ++pass) {
+        // coefficients against the j columns already in the basis
+        int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int q = w; q < j; q += nw) {
+          double a = 0.0;
+          for (int i = lane; i < m; i += 32) a += Qs[i + (size_t)q * M] * x[i];
+          a = warp_sum(a);
+          if (lane == 0) proj[q] = a;
+        }
         __syncthreads();
-        continue;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          double a = x[i];
+          for (int q = 0; q < j; ++q) a -= Qs[i + (size_t)q * M] * proj[q];
+          x[i] = a;
+        }
+        __syncthreads();
       }
-      double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
-      double nv = sqrt(a2 - x0 * x0 + v0 * v0);
-      if (threadIdx.x == 0) A[kk + (size_t)kk * M] = v0;
-      __syncthreads();
-      for (int i = kk + threadIdx.x; i < m; i += blockDim.x) A[i + (size_t)kk * M] /= nv;
-      __syncthreads();
-      int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      for (int j = kk + 1 + w; j < rn; j += nw) {
-        double dt = 0.0;
-        for (int i = kk + lane; i < m; i += 32) dt += A[i + (size_t)kk * M] * A[i + (size_t)j * M];
-        dt = warp_sum(dt);
-        for (int i = kk + lane; i < m; i += 32) A[i + (size_t)j * M] -= 2.0 * dt * A[i + (size_t)kk * M];
+      double nx = sqrt(block_sum([&] {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) a += x[i] * x[i];
+        return a;
+      }(), shs));
+      if (!(nx > 1e-8 * n0) || !(nx > 0.0)) {
+        if (threadIdx.x == 0) set_err(c.err, DERR_NUMERIC);
+        return;
       }
+      for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] /= nx;
       __syncthreads();
     }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = w; j < rn; j += nw) {
-      double* y = Qs + (size_t)j * M;
-      for (int i = lane; i < m; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
-      __syncwarp();
-      for (int kk = rn - 1; kk >= 0; --kk) {
-        double dt = 0.0;
-        for (int i = kk + lane; i < m; i += 32) dt += A[i + (size_t)kk * M] * y[i];
-        dt = warp_sum(dt);
-        for (int i = kk + lane; i < m; i += 32) y[i] -= 2.0 * dt * A[i + (size_t)kk * M];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(c.flops, 8.0 * m * (double)(rn - k) * rn);
   }
 }
 
-// L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R
-__global__ void k_cmp_lmat(LV v, Cmp c) {
-  int t = blockIdx.x, side = blockIdx.y;
+// L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R.
+// grid (tiles over r_old, tiles over rn, 2 * cnt); Lm zeroed beforehand
+__global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
+  int t = blockIdx.z >> 1, side = blockIdx.z & 1;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   const int m = v.m[b], M = v.M, rn = c.rn[t], ro = c.rold[t];
+  int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= rn || j0 >= ro) return;
   const double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
   const double* B = side == 0 ? v.u(b) : v.v(b);
   double* Lm = c.Lm + ((size_t)t * 2 + side) * v.R * v.R;
-  for (int e = threadIdx.x; e < rn * ro; e += blockDim.x) {
-    int i = e % rn, j = e / rn;
-    double acc = 0.0;
-    for (int p = 0; p < m; ++p) acc += Q[p + (size_t)i * M] * B[p + (size_t)j * M];
-    Lm[i + (size_t)j * v.R] = acc;
-  }
+  tile_gemm_64_tn(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0,
+                  ro - j0, m, 1.0);
+  if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, ro - j0) * m);
 }
 
 // row side: every block of the locals row of b is multiplied by L_b
@@ -551,9 +574,10 @@ __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
 }
 
 // row side fill-ins: M2P_bq -> A_bq += U~^T M2P_bq ; P2P_bq -> P2L_bq = U~^T P2P_bq
-// then the fill-in block is cleared.  grid (ns5, cnt)
-__global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c) {
-  int s = blockIdx.x, t = blockIdx.y;
+// (the P2L block is zero before b is eliminated).  grid (ns5 * tpc, tiles
+// over rn, cnt) with tpc column tiles per block.
+__global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
+  int s = blockIdx.x / tpc, tj = blockIdx.x % tpc, t = blockIdx.z;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   int bc[3];
@@ -562,48 +586,58 @@ __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c) {
   if (threadIdx.x == 0) sw = ws_block(v, b, s, 0, c.col);
   __syncthreads();
   if (!sw.ok) return;
-  const double* src = sw.src;
-  const int ld = sw.ld, rows = sw.rows, cols = sw.cols;
+  const int rn = c.rn[t];
+  int i0 = blockIdx.y * 64, j0 = tj * 64;
+  if (i0 >= rn || j0 >= sw.cols) return;
   int q[3];
   slot5_coords(bc, s, v.d, q);
   bool elim = colour_of(q, v.d) < c.col;
-  const int m = rows, M = v.M, rn = c.rn[t];
-  const double* Q = c.Q + ((size_t)t * 2) * M * M;
-  double* dst;
-  if (elim) dst = v.ly(b, slot6(bc, q, v.d));
-  else dst = v.lx(b, s);
-  double* srcw = const_cast<double*>(src);
-  for (int e = threadIdx.x; e < rn * cols; e += blockDim.x) {
-    int i = e % rn, j = e / rn;
-    double acc = 0.0;
-    for (int p = 0; p < m; ++p) acc += Q[p + (size_t)i * M] * src[p + (size_t)j * ld];
-    if (elim) dst[i + (size_t)j * v.R] += acc;
-    else dst[i + (size_t)j * v.R] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * cols; e += blockDim.x) {
-    int i = e % m, j = e / m;
-    srcw[i + (size_t)j * ld] = 0.0;
-  }
+  double* dst = elim ? v.ly(b, slot6(bc, q, v.d)) : v.lx(b, s);
+  const double* Q = c.Q + ((size_t)t * 2) * v.M * v.M;
+  tile_gemm_64_tn(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld, dst + i0 + (size_t)j0 * v.R, v.R,
+                  rn - i0, sw.cols - j0, sw.rows, 1.0);
+  if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, sw.cols - j0) * sw.rows);
 }
 
-// flags after the row side, U_b := U~, r_b := rn ; grid cnt
+// after the row side: clear the redirected fill-in blocks and their flags
+// (a P2P_bq leaves a pending P2L_bq for q's column side), U_b := U~,
+// r_b := rn ; grid cnt
 __global__ void k_cmp_row_done(LV v, Cmp c) {
+  __shared__ WsBlk list[128];
+  __shared__ int slots[128];
+  __shared__ int nl;
   int t = blockIdx.x;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   int bc[3], q[3];
   morton_coords(b, v.d, v.l, bc);
   const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int s = 0; s < v.ns5 && n < 128; ++s) {
+      WsBlk w = ws_block(v, b, s, 0, c.col);
+      if (!w.ok) continue;
+      list[n] = w;
+      slots[n++] = s;
+    }
+    nl = n;
+  }
+  __syncthreads();
+  for (int k = 0; k < nl; ++k) {
+    double* src = const_cast<double*>(list[k].src);
+    for (int e = threadIdx.x; e < list[k].rows * list[k].cols; e += blockDim.x) {
+      int i = e % list[k].rows, j = e / list[k].rows;
+      src[i + (size_t)j * list[k].ld] = 0.0;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0)
-    for (int s = 0; s < v.ns5; ++s) {
+    for (int k = 0; k < nl; ++k) {
+      int s = slots[k];
       slot5_coords(bc, s, v.d, q);
-      if (!in_grid(q, v.d, v.n) || cheb(bc, q, v.d) != 2) continue;
       unsigned* f = v.flag + (size_t)b * v.ns5 + s;
-      if (ldflag(f) & 1u) {
-        atomicAnd(f, ~1u);
-        if (colour_of(q, v.d) > c.col) atomicOr(f, 2u);   // a new P2L_bq waits for q's column side
-      }
+      atomicAnd(f, ~1u);
+      if (colour_of(q, v.d) > c.col) atomicOr(f, 2u);   // a new P2L_bq waits for q's column side
     }
   const double* Q = c.Q + ((size_t)t * 2) * M * M;
   for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
@@ -661,9 +695,10 @@ __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
 }
 
 // column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
-// grid (ns5, cnt)
-__global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c) {
-  int s = blockIdx.x, t = blockIdx.y;
+// (the M2P block into y_b is zero before b is eliminated).
+// grid (ns5 * tpr, tiles over rn, cnt) with tpr row tiles per block.
+__global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
+  int s = blockIdx.x / tpr, ti = blockIdx.x % tpr, t = blockIdx.z;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   int bc[3];
@@ -672,14 +707,13 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c) {
   if (threadIdx.x == 0) sw = ws_block(v, b, s, 1, c.col);
   __syncthreads();
   if (!sw.ok) return;
-  const double* src = sw.src;
-  const int ld = sw.ld, rows = sw.rows, cols = sw.cols;
+  const int rn = c.rn[t];
+  int i0 = ti * 64, j0 = blockIdx.y * 64;
+  if (i0 >= sw.rows || j0 >= rn) return;
   int q[3];
   slot5_coords(bc, s, v.d, q);
   int qb = morton_key(q, v.d, v.l);
   bool elim = colour_of(q, v.d) < c.col;
-  const int M = v.M, rn = c.rn[t];
-  const double* Q = c.Q + ((size_t)t * 2 + 1) * M * M;
   double* dst;
   int ldd;
   if (elim) {
@@ -689,35 +723,47 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c) {
     dst = v.xy(qb, slot5(q, bc, v.d));
     ldd = v.M;
   }
-  double* srcw = const_cast<double*>(src);
-  // src is rows x cols (cols = m_b); out rows x rn
-  for (int e = threadIdx.x; e < rows * rn; e += blockDim.x) {
-    int i = e % rows, j = e / rows;
-    double acc = 0.0;
-    for (int p = 0; p < cols; ++p) acc += src[i + (size_t)p * ld] * Q[p + (size_t)j * M];
-    if (elim) dst[i + (size_t)j * ldd] += acc;
-    else dst[i + (size_t)j * ldd] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-    int i = e % rows, j = e / rows;
-    srcw[i + (size_t)j * ld] = 0.0;
-  }
+  const double* Q = c.Q + ((size_t)t * 2 + 1) * v.M * v.M;
+  tile_gemm_64(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd, sw.rows - i0,
+               rn - j0, sw.cols, 1.0);
+  if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, sw.rows - i0) * (double)min(64, rn - j0) * sw.cols);
 }
 
-// flags after the column side (P2L consumed; P2P became a pending M2P of the
-// partner, which keeps bit 0) and V_b := V~ ; grid cnt
+// after the column side: clear the redirected blocks, the consumed P2L flags
+// (a P2P_qb became a pending M2P_qb, which keeps bit 0), V_b := V~ ; grid cnt
 __global__ void k_cmp_col_done(LV v, Cmp c) {
+  __shared__ WsBlk list[128];
+  __shared__ int slots[128];
+  __shared__ int nl;
   int t = blockIdx.x;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   int bc[3], q[3];
   morton_coords(b, v.d, v.l, bc);
   const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int s = 0; s < v.ns5 && n < 128; ++s) {
+      WsBlk w = ws_block(v, b, s, 1, c.col);
+      if (!w.ok) continue;
+      list[n] = w;
+      slots[n++] = s;
+    }
+    nl = n;
+  }
+  __syncthreads();
+  for (int k = 0; k < nl; ++k) {
+    double* src = const_cast<double*>(list[k].src);
+    for (int e = threadIdx.x; e < list[k].rows * list[k].cols; e += blockDim.x) {
+      int i = e % list[k].rows, j = e / list[k].rows;
+      src[i + (size_t)j * list[k].ld] = 0.0;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0)
-    for (int s = 0; s < v.ns5; ++s) {
+    for (int k = 0; k < nl; ++k) {
+      int s = slots[k];
       slot5_coords(bc, s, v.d, q);
-      if (!in_grid(q, v.d, v.n) || cheb(bc, q, v.d) != 2) continue;
       if (colour_of(q, v.d) < c.col) {
         int qb = morton_key(q, v.d, v.l);
         atomicAnd(v.flag + (size_t)qb * v.ns5 + slot5(q, bc, v.d), ~2u);
@@ -1076,6 +1122,8 @@ static int factor_level(Handle& h, int l) {
     c.col = col;
     c.cnt = cnt;
     c.eps = h.tol;
+    c.flops = h.dacc;
+    c.err = h.derr;
     c.WC = F.R + nws * F.M;
     size_t wsz = (size_t)cnt * 2 * F.M * c.WC;
     c.W = (double*)hscratch(h, 20, sizeof(double) * wsz);
@@ -1092,14 +1140,19 @@ static int factor_level(Handle& h, int l) {
     GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
     k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
-    k_cmp_qrcp<<<dim3(cnt, 2), 512, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_qrcp<<<dim3(QC * 2 * cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
-    k_cmp_lmat<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
+    AIFMM_CUDA_TRY(h, cudaMemsetAsync(c.Lm, 0, sizeof(double) * (size_t)cnt * 2 * F.R * F.R, st));
+    {
+      const int rt = (F.R + 63) / 64;
+      k_cmp_lmat<<<dim3(rt, rt, 2 * cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    }
     k_cmp_row_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
-    k_cmp_row_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    const int tpc = (F.M + 63) / 64, rtl = (F.R + 63) / 64;
+    k_cmp_row_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
     k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
     k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
-    k_cmp_col_fill<<<dim3(F.ns5, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_col_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
     k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
     delete gt;
     // ---- pivot LU
@@ -1132,7 +1185,24 @@ static int factor_level(Handle& h, int l) {
     // ---- Z = Piv^-1 B and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
     k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e); ++h.nlaunch;
-    k_lu_solve_strip<<<dim3((e.ncmax + 31) / 32, cnt), 256, 0, st>>>(e.sv); ++h.nlaunch;
+    {
+      // blocked LU solve of Z: interchanges, unit-lower blocks downwards,
+      // upper blocks upwards, each trailing update a tiled GEMM
+      const int ctiles = (e.ncmax + 63) / 64, cstr = (e.ncmax + 127) / 128;
+      k_lus_swap<<<dim3(cstr, cnt), 128, 0, st>>>(e.sv); ++h.nlaunch;
+      for (int k0 = 0; k0 < F.P; k0 += TB) {
+        k_lus_diag<1><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        if (k0 + TB < F.P) {
+          k_lus_update<1><<<dim3(ctiles, (F.P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        }
+      }
+      for (int k0 = ((F.P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
+        k_lus_diag<0><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        if (k0 > 0) {
+          k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        }
+      }
+    }
     delete gt;
     int tpb = (F.M + 63) / 64;
     gt = new GroupTimer(h, Handle::G_SCHUR);
@@ -1195,12 +1265,19 @@ int run_factor(Handle& h) {
   h.max_rank_factor = 0;
   h.flops_factor = 0;
   for (int g = 0; g < Handle::G_NG; ++g) h.g_ms[g] = h.g_flops[g] = 0, h.g_launch[g] = 0;
+  if (!h.dacc) h.dacc = hnew<double>(h, 4);
+  if (!h.dacc) return HOOM;
   for (int l = L; l >= 2; --l) {
     int e = setup_level(h, l);
     if (e) return e;
     e = factor_level(h, l);
     if (e) return e;
     collect_group_times(h);
+    double fc = 0.0;
+    AIFMM_CUDA_TRY(h, cudaMemcpy(&fc, h.dacc, sizeof(double), cudaMemcpyDeviceToHost));
+    AIFMM_CUDA_TRY(h, cudaMemset(h.dacc, 0, sizeof(double)));
+    h.g_flops[Handle::G_COMPRESS] += fc;
+    h.flops_factor += fc;
     h.flops_factor += level_flops(h, l);
   }
   // top: dense level-1 system in the level-2 multipoles

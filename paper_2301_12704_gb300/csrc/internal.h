@@ -90,6 +90,7 @@ struct Handle {
   int max_rank_nnca = 0, max_rank_factor = 0, max_m = 0;
   // launch count and optional per-kernel-group event timing (profile mode)
   long long nlaunch = 0;
+  double* dacc = nullptr;   // device flop accumulator
   bool profile = false;
   enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_NG = 4 };
   double g_ms[G_NG] = {0, 0, 0, 0};
