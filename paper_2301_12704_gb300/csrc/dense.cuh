@@ -331,3 +331,149 @@ __device__ inline void tile_gemm_64_tn(const double* A, int lda, const double* B
 }
 
 }  // namespace aifmm
+
+namespace aifmm {
+
+// panel k0..k0+LU_NB of a batched LU factored in shared memory (rows k0..n,
+// column-major with ld h = n - k0).  Warp 0 searches the pivot and swaps the
+// two panel rows; then every thread scales and updates the rows it owns.
+// Interchanges outside the panel are applied afterwards by k_lu_laswp.
+// dynamic shared memory: (maxh * LU_NB) doubles; items with n - k0 > maxh are
+// skipped here (they take the global-memory panel path).
+static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items, int k0, int maxh, int* err) {
+  extern __shared__ double Ps[];
+  __shared__ int sing;
+  LuItem it = items[blockIdx.x];
+  const int n = it.n;
+  if (k0 >= n) return;
+  const int h = n - k0;
+  if (h > maxh) return;
+  const int nbw = min(LU_NB, h);
+  double* A = it.a;
+  const int ld = it.ld;
+  for (int e = threadIdx.x; e < h * nbw; e += blockDim.x) {
+    int i = e % h, j = e / h;
+    Ps[i + (size_t)j * h] = A[(k0 + i) + (size_t)(k0 + j) * ld];
+  }
+  if (threadIdx.x == 0) sing = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int jj = 0; jj < nbw; ++jj) {
+    if (threadIdx.x < 32) {
+      double bv = -1.0;
+      int bi = -1;
+      for (int i = jj + lane; i < h; i += 32) {
+        double x = fabs(Ps[i + (size_t)jj * h]);
+        if (x > bv) {
+          bv = x;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      double cm = it.colmax ? it.colmax[k0 + jj] : 0.0;
+      if (!(bv > 1e-14 * cm) || !(bv > 0.0)) {
+        if (lane == 0) sing = 1;
+      } else {
+        if (lane == 0) it.ipiv[k0 + jj] = k0 + bi;
+        if (bi != jj && lane < nbw) {
+          double x = Ps[jj + (size_t)lane * h];
+          Ps[jj + (size_t)lane * h] = Ps[bi + (size_t)lane * h];
+          Ps[bi + (size_t)lane * h] = x;
+        }
+      }
+    }
+    __syncthreads();
+    if (sing) {
+      if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
+      return;
+    }
+    const double piv = Ps[jj + (size_t)jj * h];
+    for (int i = jj + 1 + threadIdx.x; i < h; i += blockDim.x) {
+      double l = Ps[i + (size_t)jj * h] / piv;
+      Ps[i + (size_t)jj * h] = l;
+      for (int cc = jj + 1; cc < nbw; ++cc) Ps[i + (size_t)cc * h] -= l * Ps[jj + (size_t)cc * h];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < h * nbw; e += blockDim.x) {
+    int i = e % h, j = e / h;
+    A[(k0 + i) + (size_t)(k0 + j) * ld] = Ps[i + (size_t)j * h];
+  }
+}
+
+// the panel's interchanges applied to every column outside the panel
+// (left: the L factor, right: the part still to be factored); grid (colchunks, items)
+static __global__ void __launch_bounds__(128) k_lu_laswp(const LuItem* items, int k0, int maxh) {
+  LuItem it = items[blockIdx.y];
+  const int n = it.n;
+  if (k0 >= n || n - k0 > maxh) return;
+  const int nbw = min(LU_NB, n - k0);
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || (c >= k0 && c < k0 + nbw)) return;
+  double* col = it.a + (size_t)c * it.ld;
+  for (int jj = 0; jj < nbw; ++jj) {
+    int p = it.ipiv[k0 + jj];
+    if (p != k0 + jj) {
+      double x = col[k0 + jj];
+      col[k0 + jj] = col[p];
+      col[p] = x;
+    }
+  }
+}
+
+// global-memory panel for items too tall for shared memory
+static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items, int k0, int maxh, int* err) {
+  LuItem it = items[blockIdx.x];
+  if (k0 >= it.n || it.n - k0 <= maxh) return;
+  // same algorithm as k_lu_panel, full-row interchanges
+  __shared__ double shv[32];
+  __shared__ int shi[32];
+  int n = it.n;
+  double* A = it.a;
+  const int ld = it.ld;
+  int kend = min(n, k0 + LU_NB);
+  for (int j = k0; j < kend; ++j) {
+    ArgMax best;
+    best.v = -1.0;
+    best.i = -1;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      ArgMax c;
+      c.v = fabs(A[i + (size_t)j * ld]);
+      c.i = i;
+      best = amax_pick(best, c);
+    }
+    best = block_amax(best, shv, shi);
+    int p = best.i;
+    double cm = it.colmax ? it.colmax[j] : 0.0;
+    if (!(best.v > 1e-14 * cm) || !(best.v > 0.0)) {
+      if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
+      return;
+    }
+    if (threadIdx.x == 0) it.ipiv[j] = p;
+    if (p != j)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double t = A[j + (size_t)c * ld];
+        A[j + (size_t)c * ld] = A[p + (size_t)c * ld];
+        A[p + (size_t)c * ld] = t;
+      }
+    __syncthreads();
+    double piv = A[j + (size_t)j * ld];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (size_t)j * ld] /= piv;
+    __syncthreads();
+    int w = kend - j - 1, hh = n - j - 1;
+    for (int e = threadIdx.x; e < w * hh; e += blockDim.x) {
+      int i = j + 1 + e % hh, c = j + 1 + e / hh;
+      A[i + (size_t)c * ld] -= A[i + (size_t)j * ld] * A[j + (size_t)c * ld];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace aifmm

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 
 #include <cooperative_groups.h>
 
@@ -314,17 +315,17 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 // Householder QR with column pivoting; the first nf = r_b columns are taken
 // in order, then the largest residual column among the fill-ins while its
 // norm exceeds eps * max_j ||F_j||.  Produces Q[:, :rank] explicitly.
-// One thread-block cluster of QC CTAs per (box, side): CTA c updates the
+// One thread-block cluster of QC CTAs per (box, side) (QC chosen per level
+// by the host so that the colour's clusters fill the GPU): CTA c updates the
 // trailing columns j with j % QC == c; the pivot is reduced across the
 // cluster through distributed shared memory; CTA 0 swaps columns and builds
 // each reflector.  Every CTA derives the loop exit from the same cluster-wide
 // values, so all of them pass the same sequence of cluster barriers.
-// grid (QC * 2 * cnt), 256 threads.
-constexpr int QC = 8;
-
-__global__ void __cluster_dims__(QC, 1, 1) __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
+// grid (QC * 2 * cnt), 256 threads, launched with cluster size QC.
+__global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
+  const int QC = (int)cl.num_blocks();
   __shared__ double shv[32];
   __shared__ int shi[32];
   __shared__ double shs[32];
@@ -421,19 +422,19 @@ __global__ void __cluster_dims__(QC, 1, 1) __launch_bounds__(256) k_cmp_qrcp(LV 
     cl.sync();
     // apply H_k to the trailing columns owned by this CTA, refresh norms
     int j0 = (k + 1) + ((cr - (k + 1) % QC) + QC) % QC;
-    for (int j = j0 + QC * w; j < n; j += QC * nw) {
-      double dt = 0.0;
-      for (int i = k + lane; i < m; i += 32) dt += W[i + (size_t)k * M] * W[i + (size_t)j * M];
-      dt = warp_sum(dt);
-      double nn = 0.0;
-      for (int i = k + lane; i < m; i += 32) {
-        double x = W[i + (size_t)j * M] - 2.0 * dt * W[i + (size_t)k * M];
-        W[i + (size_t)j * M] = x;
-        if (i > k) nn += x * x;
+      for (int j = j0 + QC * w; j < n; j += QC * nw) {
+        double dt = 0.0;
+        for (int i = k + lane; i < m; i += 32) dt += W[i + (size_t)k * M] * W[i + (size_t)j * M];
+        dt = warp_sum(dt);
+        double nn = 0.0;
+        for (int i = k + lane; i < m; i += 32) {
+          double x = W[i + (size_t)j * M] - 2.0 * dt * W[i + (size_t)k * M];
+          W[i + (size_t)j * M] = x;
+          if (i > k) nn += x * x;
+        }
+        nn = warp_sum(nn);
+        if (lane == 0) cn[j] = nn;
       }
-      nn = warp_sum(nn);
-      if (lane == 0) cn[j] = nn;
-    }
     cl.sync();
   }
   cl.sync();   // no CTA leaves while another may still read its shared memory
@@ -1095,6 +1096,50 @@ struct GroupTimer {
   }
 };
 
+// optional per-region timing (environment AIFMM_PROFILE_DETAIL=1): event
+// pairs around named regions of the colour loop, summed per level and
+// printed to stderr; a diagnostic, off by default
+struct DetailProf {
+  bool on = false;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  cudaEvent_t cur;
+  std::string name;
+  cudaStream_t st;
+  void begin(const char* n) {
+    if (!on) return;
+    cudaEventCreate(&cur);
+    cudaEventRecord(cur, st);
+    name = n;
+  }
+  void end() {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back({name, {cur, e}});
+  }
+  void report(int l) {
+    if (!on) return;
+    std::vector<std::pair<std::string, double>> tot;
+    for (auto& x : ev) {
+      float ms = 0.f;
+      cudaEventSynchronize(x.second.second);
+      cudaEventElapsedTime(&ms, x.second.first, x.second.second);
+      bool f = false;
+      for (auto& t : tot)
+        if (t.first == x.first) {
+          t.second += ms;
+          f = true;
+        }
+      if (!f) tot.push_back({x.first, ms});
+      cudaEventDestroy(x.second.first);
+      cudaEventDestroy(x.second.second);
+    }
+    ev.clear();
+    for (auto& t : tot) std::fprintf(stderr, "DETAIL l=%d %-16s %9.3f ms\n", l, t.first.c_str(), t.second);
+  }
+};
+
 static void collect_group_times(Handle& h) {
   for (auto& e : h.g_ev) {
     float ms = 0.f;
@@ -1114,6 +1159,9 @@ static int factor_level(Handle& h, int l) {
   LV v = view(h, F);
   const int ncol = ipow(3, d);
   int nws = ipow(5, d) - ipow(3, d);
+  DetailProf dp;
+  dp.on = std::getenv("AIFMM_PROFILE_DETAIL") != nullptr;
+  dp.st = st;
   for (int col = 0; col < ncol; ++col) {
     int cnt = colour_count(col, d, F.n);
     if (cnt == 0) continue;
@@ -1138,22 +1186,60 @@ static int factor_level(Handle& h, int l) {
     c.rold = ib + 5 * cnt;
     c.skip = ib + 6 * cnt;
     GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
+    dp.begin("gather");
     k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
-    k_cmp_qrcp<<<dim3(QC * 2 * cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.begin("qrcp");
+    {
+      // one cluster of qc CTAs per box side (skipped boxes exit at once);
+      // qc so that the colour's clusters give about two CTAs per SM
+      int qc = 2;
+      while (qc < 16 && qc * 2 * cnt < 2 * h.nsm) qc *= 2;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(qc * 2 * cnt);
+      cfg.blockDim = dim3(256);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = qc;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, c));
+      ++h.nlaunch;
+    }
+    dp.end();
+    dp.begin("equalise");
     k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
+    dp.begin("lmat");
     AIFMM_CUDA_TRY(h, cudaMemsetAsync(c.Lm, 0, sizeof(double) * (size_t)cnt * 2 * F.R * F.R, st));
     {
       const int rt = (F.R + 63) / 64;
       k_cmp_lmat<<<dim3(rt, rt, 2 * cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     }
+    dp.end();
+    dp.begin("row_transform");
     k_cmp_row_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
+    dp.begin("row_fill");
     const int tpc = (F.M + 63) / 64, rtl = (F.R + 63) / 64;
     k_cmp_row_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
+    dp.end();
+    dp.begin("row_done");
     k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
+    dp.begin("col_transform");
     k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
+    dp.begin("col_fill");
     k_cmp_col_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
+    dp.end();
+    dp.begin("col_done");
     k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    dp.end();
     delete gt;
     // ---- pivot LU
     Elim e;
@@ -1173,21 +1259,36 @@ static int factor_level(Handle& h, int l) {
     e.totc = eb + 2 * cnt;
     k_coupled<<<(cnt + 127) / 128, 128, 0, st>>>(v, e); ++h.nlaunch;
     gt = new GroupTimer(h, Handle::G_PIVLU);
+    dp.begin("piv_build");
     k_piv_build<<<cnt, 256, 0, st>>>(v, e); ++h.nlaunch;
+    dp.end();
     k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P); ++h.nlaunch;
-    for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
-      k_lu_panel<<<cnt, 256, 0, st>>>(e.lu, k0, h.derr); ++h.nlaunch;
-      k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
-      int tiles = (F.P + 63) / 64;
-      k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
+    dp.begin("lu");
+    {
+      const int maxh = h.panel_rows;
+      for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
+        const int hh = std::min(F.P - k0, maxh);
+        k_lu_panel_sm<<<cnt, 256, sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
+        if (F.P - k0 > maxh) {
+          k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
+        }
+        k_lu_laswp<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
+        k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
+        int tiles = (F.P + 63) / 64;
+        k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
+      }
     }
+    dp.end();
     delete gt;
     // ---- Z = Piv^-1 B and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
+    dp.begin("z_build");
     k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e); ++h.nlaunch;
+    dp.end();
     {
       // blocked LU solve of Z: interchanges, unit-lower blocks downwards,
       // upper blocks upwards, each trailing update a tiled GEMM
+      dp.begin("lus");
       const int ctiles = (e.ncmax + 63) / 64, cstr = (e.ncmax + 127) / 128;
       k_lus_swap<<<dim3(cstr, cnt), 128, 0, st>>>(e.sv); ++h.nlaunch;
       for (int k0 = 0; k0 < F.P; k0 += TB) {
@@ -1202,11 +1303,14 @@ static int factor_level(Handle& h, int l) {
           k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
         }
       }
+      dp.end();
     }
     delete gt;
     int tpb = (F.M + 63) / 64;
     gt = new GroupTimer(h, Handle::G_SCHUR);
+    dp.begin("schur");
     k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb); ++h.nlaunch;
+    dp.end();
     delete gt;
     AIFMM_CUDA_TRY(h, cudaGetLastError());
   }
@@ -1218,6 +1322,7 @@ static int factor_level(Handle& h, int l) {
             (er == DERR_SINGULAR ? ": singular pivot block" : " (device error " + std::to_string(er) + ")");
     return er == DERR_SINGULAR ? HSINGULAR : HCAPACITY;
   }
+  dp.report(l);
   k_xoff<<<(F.nb + 127) / 128, 128, 0, st>>>(F.nb, d, F.r, F.xoff); ++h.nlaunch;
   for (int b = 0; b < F.nb; ++b) h.max_rank_factor = std::max(h.max_rank_factor, F.h_r[b]);
   return HOK;
@@ -1267,6 +1372,22 @@ int run_factor(Handle& h) {
   for (int g = 0; g < Handle::G_NG; ++g) h.g_ms[g] = h.g_flops[g] = 0, h.g_launch[g] = 0;
   if (!h.dacc) h.dacc = hnew<double>(h, 4);
   if (!h.dacc) return HOOM;
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  {
+    // tallest LU panel kept in shared memory: (rows x 32) doubles within the
+    // opt-in limit of the device
+    int smax = 0;
+    AIFMM_CUDA_TRY(h, cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h.device));
+    h.panel_rows = (smax - 1024) / (int)(sizeof(double) * LU_NB);
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lu_panel_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * (size_t)h.panel_rows * LU_NB)));
+  }
+  AIFMM_CUDA_TRY(h, cudaDeviceGetAttribute(&h.nsm, cudaDevAttrMultiProcessorCount, h.device));
+  {
+    int l2 = 0;
+    AIFMM_CUDA_TRY(h, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h.device));
+    h.l2_bytes = (size_t)l2;
+  }
   for (int l = L; l >= 2; --l) {
     int e = setup_level(h, l);
     if (e) return e;
@@ -1304,7 +1425,12 @@ int run_factor(Handle& h) {
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(it, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
   k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
-    k_lu_panel<<<1, 256, 0, st>>>(it, k0, h.derr); ++h.nlaunch;
+    const int hh = std::min(h.ntop - k0, h.panel_rows);
+    k_lu_panel_sm<<<1, 256, sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
+    if (h.ntop - k0 > h.panel_rows) {
+      k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
+    }
+    k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
     k_lu_trsm<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
     k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;

@@ -63,6 +63,9 @@ struct Handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
+  int nsm = 152;
+  int panel_rows = 0;   // tallest LU panel factored in shared memory
+  size_t l2_bytes = 0;
   // tree
   double* pts = nullptr;      // SoA [d][N] in tree order
   int* perm = nullptr;        // [N] tree position -> original index
