@@ -75,6 +75,11 @@ typedef struct {
   void* stream;    /* cudaStream_t to run on; NULL = the library's own stream */
   int profile;     /* 1: time the factorisation's kernel groups with CUDA events
                       on the handle's stream (reported by aifmm_stats) */
+  int no_symmetry; /* 0 (default): use A = A^T (every built-in kernel is symmetric
+                      and sources = targets, so V = U, Sec. 2.3): one RRQR per box
+                      gives both bases and the Schur update computes each pair of
+                      mirrored blocks once; 1: the general elimination, which
+                      compresses rows and columns separately and updates every block */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of

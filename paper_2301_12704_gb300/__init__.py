@@ -38,7 +38,8 @@ class Kernel(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
+    _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
+                ("no_symmetry", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -114,13 +115,16 @@ class Handle:
 
 
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
-                depth: int = 0, stream=None, profile: bool = False) -> Handle:
-    """Build tree, lists, NNCA operators and the extended system (C: aifmm_build)."""
+                depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True) -> Handle:
+    """Build tree, lists, NNCA operators and the extended system (C: aifmm_build).
+
+    ``symmetric=False`` selects the general elimination (rows and columns
+    compressed separately, every Schur block computed)."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
-    o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)))
+    o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric))
     out = C.c_void_p()
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))

@@ -207,7 +207,15 @@ struct Cmp {
   double eps;
   double* flops;       // device accumulator of algorithmic flops (compress group)
   int* err;
+  int sym;             // 1: A = A^T, side 1 is never gathered or factored and
+                       // V~_b = U~_b (the column fill-ins are the transposed row
+                       // fill-ins, so both RRQRs would see the same matrix)
 };
+
+// basis of one side; with sym both sides read the side-0 basis
+__device__ inline double* qbase(const Cmp& c, int t, int side, int M) {
+  return c.Q + ((size_t)t * 2 + (c.sym ? 0 : side)) * M * M;
+}
 
 // fill-in flags are read with a load that bypasses the non-coherent cache
 // path; they are only ever modified with atomics
@@ -309,7 +317,7 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
   if (t >= c.cnt) return;
   int b = cbox(c, v, t);
   int rb = v.r[b];
-  c.skip[t] = (v.m[b] == 0 || (c.nc[2 * t] == rb && c.nc[2 * t + 1] == rb)) ? 1 : 0;
+  c.skip[t] = (v.m[b] == 0 || (c.nc[2 * t] == rb && (c.sym || c.nc[2 * t + 1] == rb))) ? 1 : 0;
 }
 
 // Householder QR with column pivoting; the first nf = r_b columns are taken
@@ -321,7 +329,8 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 // cluster through distributed shared memory; CTA 0 swaps columns and builds
 // each reflector.  Every CTA derives the loop exit from the same cluster-wide
 // values, so all of them pass the same sequence of cluster barriers.
-// grid (QC * 2 * cnt), 256 threads, launched with cluster size QC.
+// With sym only side 0 is factored and its rank serves both sides.
+// grid (QC * sides * cnt), 256 threads, launched with cluster size QC.
 __global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -333,7 +342,7 @@ __global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   __shared__ double lmax;
   const int cr = (int)cl.block_rank();
   const int bs = blockIdx.x / QC;
-  const int t = bs >> 1, side = bs & 1;
+  const int t = c.sym ? bs : bs >> 1, side = c.sym ? 0 : bs & 1;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
   const int m = v.m[b], n = c.nc[t * 2 + side], nf = c.rold[t];
@@ -454,6 +463,7 @@ __global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   }
   if (cr == 0 && threadIdx.x == 0) {
     c.rk[t * 2 + side] = rank;
+    if (c.sym) c.rk[t * 2 + 1] = rank;
     double f = 2.0 * m * (n - nf);
     for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
     atomicAdd(c.flops, f);
@@ -529,7 +539,7 @@ __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   const int m = v.m[b], M = v.M, rn = c.rn[t], ro = c.rold[t];
   int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (i0 >= rn || j0 >= ro) return;
-  const double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
+  const double* Q = qbase(c, t, side, M);
   const double* B = side == 0 ? v.u(b) : v.v(b);
   double* Lm = c.Lm + ((size_t)t * 2 + side) * v.R * v.R;
   tile_gemm_64_tn(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0,
@@ -724,7 +734,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
     dst = v.xy(qb, slot5(q, bc, v.d));
     ldd = v.M;
   }
-  const double* Q = c.Q + ((size_t)t * 2 + 1) * v.M * v.M;
+  const double* Q = qbase(c, t, 1, v.M);
   tile_gemm_64(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd, sw.rows - i0,
                rn - j0, sw.cols, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, sw.rows - i0) * (double)min(64, rn - j0) * sw.cols);
@@ -770,7 +780,7 @@ __global__ void k_cmp_col_done(LV v, Cmp c) {
         atomicAnd(v.flag + (size_t)qb * v.ns5 + slot5(q, bc, v.d), ~2u);
       }
     }
-  const double* Q = c.Q + ((size_t)t * 2 + 1) * M * M;
+  const double* Q = qbase(c, t, 1, M);
   for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
     int i = e % m, j = e / m;
     v.v(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
@@ -908,13 +918,31 @@ __global__ void k_z_build(LV v, Elim e) {
   }
 }
 
+// storage of the block (row entity R, column entity C); pc, qc their boxes' coordinates
+__device__ inline double* schur_target(const LV& v, int rbox, int rtype, int ctype, const int* pc, const int* qc,
+                                       int& ldt) {
+  if (rtype == 0) {
+    int s = slot5(pc, qc, v.d);
+    ldt = v.M;
+    return ctype == 0 ? v.xx(rbox, s) : v.xy(rbox, s);
+  }
+  ldt = v.R;
+  return ctype == 0 ? v.lx(rbox, slot5(pc, qc, v.d)) : v.ly(rbox, slot6(pc, qc, v.d));
+}
+
 // Schur update of every coupled block; 64x64 tiles.
 // grid (MAXC * tpb, MAXC * tpb, cnt) with tpb = tiles per block side.
-__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb) {
+// The row and column lists name the same entities in the same order
+// (X_p <-> x_p, Lc_p <-> y_p, Lc_b <-> y_b), so with sym (A = A^T, which the
+// elimination keeps: Piv and the Schur complement stay symmetric) the block
+// (j, i) is the transpose of (i, j): only i <= j is computed and each
+// off-diagonal tile is also stored transposed at its mirror.
+__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   int t = blockIdx.z;
   int ri = blockIdx.y / tpb, ti = blockIdx.y % tpb;
   int cj = blockIdx.x / tpb, tj = blockIdx.x % tpb;
   if (ri >= e.nrow[t] || cj >= e.ncol[t]) return;
+  if (sym && ri > cj) return;
   Coupled R = e.rows[(size_t)t * MAXC + ri];
   Coupled C = e.cols[(size_t)t * MAXC + cj];
   int i0 = ti * 64, j0 = tj * 64;
@@ -926,23 +954,8 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb) {
   morton_coords(R.box, v.d, v.l, pc);
   morton_coords(C.box, v.d, v.l, qc);
   const double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)(C.off + j0) * P;
-  // target block
-  double* T;
   int ldt;
-  bool colx = C.type == 0;
-  if (R.type == 0) {
-    int s = slot5(pc, qc, v.d);
-    T = colx ? v.xx(R.box, s) : v.xy(R.box, s);
-    ldt = v.M;
-  } else {
-    if (colx) {
-      T = v.lx(R.box, slot5(pc, qc, v.d));
-    } else {
-      T = v.ly(R.box, slot6(pc, qc, v.d));
-    }
-    ldt = v.R;
-  }
-  T += i0 + (size_t)j0 * ldt;
+  double* T = schur_target(v, R.box, R.type, C.type, pc, qc, ldt) + i0 + (size_t)j0 * ldt;
   int mr = min(64, R.size - i0), nc = min(64, C.size - j0);
   if (R.type == 2) {
     // (Lc_b, C) += Z[m + i, C]
@@ -958,9 +971,21 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb) {
   tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   // a block between well-separated boxes is a pending fill-in unless both
   // boxes are eliminated (an M2L fill-in, kept without compression)
-  if (threadIdx.x == 0 && ti == 0 && tj == 0 && C.type != 2 && !(R.type == 1 && C.type == 1) &&
-      cheb(pc, qc, v.d) == 2)
+  const bool ws = C.type != 2 && !(R.type == 1 && C.type == 1) && cheb(pc, qc, v.d) == 2;
+  if (threadIdx.x == 0 && ti == 0 && tj == 0 && ws)
     atomicOr(v.flag + (size_t)R.box * v.ns5 + slot5(pc, qc, v.d), R.type == 0 ? 1u : 2u);
+  if (sym && ri < cj) {
+    // mirror: row entity of C, column entity of R (R is never Lc_b here)
+    __syncthreads();
+    int ldm;
+    double* Tm = schur_target(v, C.box, C.type, R.type, qc, pc, ldm) + j0 + (size_t)i0 * ldm;
+    for (int x = threadIdx.x; x < mr * nc; x += blockDim.x) {
+      int j = x % nc, i = x / nc;
+      Tm[j + (size_t)i * ldm] = T[i + (size_t)j * ldt];
+    }
+    if (threadIdx.x == 0 && ti == 0 && tj == 0 && ws)
+      atomicOr(v.flag + (size_t)C.box * v.ns5 + slot5(qc, pc, v.d), C.type == 0 ? 1u : 2u);
+  }
 }
 
 // ============================ top (level-1 system) ===========================
@@ -1172,6 +1197,8 @@ static int factor_level(Handle& h, int l) {
     c.eps = h.tol;
     c.flops = h.dacc;
     c.err = h.derr;
+    c.sym = h.sym ? 1 : 0;
+    const int nsides = h.sym ? 1 : 2;
     c.WC = F.R + nws * F.M;
     size_t wsz = (size_t)cnt * 2 * F.M * c.WC;
     c.W = (double*)hscratch(h, 20, sizeof(double) * wsz);
@@ -1187,7 +1214,7 @@ static int factor_level(Handle& h, int l) {
     c.skip = ib + 6 * cnt;
     GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
     dp.begin("gather");
-    k_cmp_gather<<<dim3(cnt, 2), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_gather<<<dim3(cnt, nsides), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
     dp.begin("qrcp");
@@ -1195,9 +1222,9 @@ static int factor_level(Handle& h, int l) {
       // one cluster of qc CTAs per box side (skipped boxes exit at once);
       // qc so that the colour's clusters give about two CTAs per SM
       int qc = 2;
-      while (qc < 16 && qc * 2 * cnt < 2 * h.nsm) qc *= 2;
+      while (qc < 16 && qc * nsides * cnt < 2 * h.nsm) qc *= 2;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(qc * 2 * cnt);
+      cfg.gridDim = dim3(qc * nsides * cnt);
       cfg.blockDim = dim3(256);
       cfg.stream = st;
       cudaLaunchAttribute at[1];
@@ -1309,7 +1336,7 @@ static int factor_level(Handle& h, int l) {
     int tpb = (F.M + 63) / 64;
     gt = new GroupTimer(h, Handle::G_SCHUR);
     dp.begin("schur");
-    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb); ++h.nlaunch;
+    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb, h.sym ? 1 : 0); ++h.nlaunch;
     dp.end();
     delete gt;
     AIFMM_CUDA_TRY(h, cudaGetLastError());
@@ -1341,7 +1368,7 @@ static double level_flops(Handle& h, int l) {
     int cb = colour_of(bc, d);
     double m = F.h_m[b], r = F.h_r[b], n = m + r;
     if (m == 0) continue;
-    double rows = r, cols = r;
+    double rows = r, cols = r, ssq = 0.0;
     for (int o = 0; o < ipow(3, d); ++o) {
       int oo = o;
       for (int k = 0; k < d; ++k) {
@@ -1353,8 +1380,14 @@ static double level_flops(Handle& h, int l) {
       double sz = colour_of(q, d) < cb ? F.h_r[qb] : F.h_m[qb];
       rows += sz;
       cols += sz;
+      ssq += sz * sz;
     }
     double flu = 2.0 / 3.0 * n * n * n, fz = 2.0 * n * n * cols, fs = 2.0 * (rows - r) * m * cols;
+    if (h.sym) {
+      // blocks (i, j) with i <= j only: neighbour pairs and the y_b column
+      double sn = rows - r;
+      fs = 2.0 * m * (0.5 * (sn * sn + ssq) + sn * r);
+    }
     h.g_flops[Handle::G_PIVLU] += flu;
     h.g_flops[Handle::G_ZSOLVE] += fz;
     h.g_flops[Handle::G_SCHUR] += fs;

@@ -95,6 +95,7 @@ struct Handle {
   long long nlaunch = 0;
   double* dacc = nullptr;   // device flop accumulator
   bool profile = false;
+  bool sym = true;      // A = A^T exploited by the factorisation
   enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_NG = 4 };
   double g_ms[G_NG] = {0, 0, 0, 0};
   double g_flops[G_NG] = {0, 0, 0, 0};

@@ -72,16 +72,30 @@ def test_tree_and_nnca_match_oracle(A, w):
     assert same >= 0.97 * total, (same, total)
 
 
+_ORACLE_X = {}
+
+
+def _oracle_solution(w, pts, b):
+    """Oracle (colour order) and dense solutions of one case, computed once."""
+    if w.name not in _ORACLE_X:
+        T, K, nn = _oracle(w, pts)
+        xo = _to_orig(T, OF.solve(OF.factor(T, K, nn, w.tol, order="colour"), b[T.perm]))
+        _ORACLE_X[w.name] = (xo, np.linalg.solve(K.dense(pts), b))
+    return _ORACLE_X[w.name]
+
+
+@pytest.mark.parametrize("symmetric", [True, False], ids=["sym", "general"])
 @pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
-def test_factor_solve_matches_oracle(A, w):
+def test_factor_solve_matches_oracle(A, w, symmetric):
+    """Both elimination modes against the oracle's general elimination: the
+    symmetric mode (one RRQR per box, mirrored Schur blocks) differs from it
+    only by rounding and the RRQR cut-off, so the same 10 tol bound holds."""
     pts, b = W.points_and_rhs(w, nrhs=2)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length)
+    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, symmetric=symmetric)
     A.aifmm_factor(h)
     x = A.aifmm_solve(h, b)
-    T, K, nn = _oracle(w, pts)
-    xo = _to_orig(T, OF.solve(OF.factor(T, K, nn, w.tol, order="colour"), b[T.perm]))
+    xo, xd = _oracle_solution(w, pts, b)
     assert _rel(x, xo) <= 10 * w.tol
-    xd = np.linalg.solve(K.dense(pts), b)
     assert _rel(x, xd) <= 100 * w.tol
 
 
