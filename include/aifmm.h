@@ -80,6 +80,10 @@ typedef struct {
                       gives both bases and the Schur update computes each pair of
                       mirrored blocks once; 1: the general elimination, which
                       compresses rows and columns separately and updates every block */
+  double factor_tol; /* > 0: RRQR threshold of the compress-and-redirect steps, in
+                      place of tol (the NNCA operators and aifmm_matvec keep tol);
+                      a looser value gives the low-accuracy factorisation used as a
+                      GMRES preconditioner (Sec. 4, Experiment 5). 0: tol */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of
@@ -157,6 +161,23 @@ aifmm_status aifmm_matvec(aifmm_h h, const double* x, double* y, int nrhs, int64
 /* y = A x with every entry of A evaluated (exact O(N^2) direct sum on the
  * GPU); used to measure true residuals. Errors: STATE, INVALID, OOM, CUDA. */
 aifmm_status aifmm_direct_matvec(aifmm_h h, const double* x, double* y, int nrhs, int64_t ld);
+
+/* Restarted GMRES (Sec. 4: the iterative solver of Experiments 2-4, with the
+ * NNCA H^2 product; Experiment 5: a low-accuracy AIFMM factorisation as the
+ * preconditioner).  Solves A_H2 x = b with right preconditioning M^-1 = the
+ * AIFMM solve (Algorithm 3) when use_precond != 0, none otherwise; starts
+ * from x = 0; stops when ||b - A_H2 x|| / ||b|| <= rtol (the residual is
+ * recomputed with a product after each restart cycle) or after maxit
+ * iterations.  Arnoldi uses classical Gram-Schmidt applied twice.
+ *   b, x      N-vectors (host or device), original order; x is output only.
+ *   rtol      >= 0; maxit >= 1 total iterations (products); 1 <= restart <= 512.
+ *   iters     (may be NULL) iterations done; relres (may be NULL) the final
+ *             relative residual of the H^2 system.
+ * Device memory: N * (restart + 3) doubles of handle scratch.
+ * Errors: STATE (no build, or use_precond without factor), INVALID, NOCONV
+ * (x and relres hold the last iterate), OOM, CUDA. */
+aifmm_status aifmm_gmres(aifmm_h h, const double* b, double* x, double rtol, int maxit, int restart,
+                         int use_precond, int* iters, double* relres);
 
 /* Statistics of the handle. */
 aifmm_status aifmm_stats(aifmm_h h, aifmm_stats_t* out);

@@ -39,7 +39,7 @@ class Kernel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("no_symmetry", C.c_int)]
+                ("no_symmetry", C.c_int), ("factor_tol", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -70,6 +70,7 @@ def lib():
         L.aifmm_noalloc_scratch_bytes.restype = i64
         L.aifmm_matvec.argtypes = [vp, vp, vp, cint, i64]
         L.aifmm_direct_matvec.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_gmres.argtypes = [vp, vp, vp, dbl, cint, cint, cint, C.POINTER(cint), C.POINTER(dbl)]
         L.aifmm_stats.argtypes = [vp, C.POINTER(Stats)]
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
         L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
@@ -80,7 +81,7 @@ def lib():
         L.aifmm_destroy.argtypes = [vp]
         L.aifmm_destroy.restype = None
         for name in ("aifmm_build", "aifmm_factor", "aifmm_solve", "aifmm_solve_noalloc", "aifmm_matvec",
-                     "aifmm_direct_matvec",
+                     "aifmm_direct_matvec", "aifmm_gmres",
                      "aifmm_stats", "aifmm_tree_perm", "aifmm_level_ranks", "aifmm_level_pivots",
                      "aifmm_levels"):
             getattr(L, name).restype = C.c_int
@@ -115,16 +116,19 @@ class Handle:
 
 
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
-                depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True) -> Handle:
+                depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True,
+                factor_tol: float = 0.0) -> Handle:
     """Build tree, lists, NNCA operators and the extended system (C: aifmm_build).
 
     ``symmetric=False`` selects the general elimination (rows and columns
-    compressed separately, every Schur block computed)."""
+    compressed separately, every Schur block computed); ``factor_tol`` > 0 is
+    the compress threshold of the factorisation (default: ``tol``)."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
-    o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric))
+    o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
+                float(factor_tol))
     out = C.c_void_p()
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
@@ -194,6 +198,33 @@ def aifmm_matvec(h: Handle, x):
 def aifmm_direct_matvec(h: Handle, x):
     """y = A x, every entry evaluated (C: aifmm_direct_matvec)."""
     return _product(lib().aifmm_direct_matvec, h, x)
+
+
+def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: int = 50,
+                use_precond: bool = True, raise_noconv: bool = True):
+    """Restarted GMRES on the H^2 product, right-preconditioned by the AIFMM
+    factorisation when ``use_precond`` (C: aifmm_gmres).  Returns
+    (x, iterations, relative residual); x has b's type and device."""
+    if isinstance(b, np.ndarray):
+        bb = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        x = np.empty_like(bb)
+    else:
+        bb = b.reshape(-1).contiguous()
+        x = torch_empty_like(bb)
+    pb, kb = _ptr(bb)
+    px, kx = _ptr(x)
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = lib().aifmm_gmres(h.raw, C.c_void_p(pb), C.c_void_p(px), float(rtol), int(maxit), int(restart),
+                           int(bool(use_precond)), C.byref(it), C.byref(rr))
+    if st != 0 and (st != 5 or raise_noconv):
+        _check(st, h.raw)
+    return x, it.value, rr.value
+
+
+def torch_empty_like(t):
+    import torch
+    return torch.empty_like(t)
 
 
 def aifmm_stats(h: Handle) -> dict:

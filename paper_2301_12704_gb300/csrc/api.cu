@@ -100,6 +100,7 @@ static aifmm_status to_status(int e) {
     case HOOM: return AIFMM_ERR_OOM;
     case HSINGULAR: return AIFMM_ERR_SINGULAR;
     case HSTATE: return AIFMM_ERR_STATE;
+    case HNOCONV: return AIFMM_ERR_NOCONV;
     case HCAPACITY: return AIFMM_ERR_CAPACITY;
     default: return AIFMM_ERR_CUDA;
   }
@@ -142,7 +143,8 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   if (!points || !k || !out || n < 1 || n > (int64_t)1 << 30 || (k->dim != 2 && k->dim != 3) ||
       !(tol >= 0.0) || leaf_size < 1 || k->kind < 0 || k->kind > 3 || !std::isfinite(k->diag) ||
       (k->kind == AIFMM_K_GAUSS && !(k->length > 0.0)) || (opt && opt->order != 0) ||
-      (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12))) {
+      (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12)) ||
+      (opt && !(opt->factor_tol >= 0.0 && std::isfinite(opt->factor_tol)))) {
     g_build_err = "invalid argument";
     return AIFMM_ERR_INVALID;
   }
@@ -152,6 +154,7 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.N = n;
   h.d = k->dim;
   h.tol = tol;
+  h.ftol = (opt && opt->factor_tol > 0.0) ? opt->factor_tol : tol;
   h.leaf = leaf_size;
   h.kp.kind = k->kind;
   h.kp.dim = k->dim;
@@ -362,6 +365,43 @@ aifmm_status aifmm_matvec(aifmm_h c, const double* x, double* y, int nrhs, int64
 
 aifmm_status aifmm_direct_matvec(aifmm_h c, const double* x, double* y, int nrhs, int64_t ld) {
   return product(c, x, y, nrhs, ld, true);
+}
+
+aifmm_status aifmm_gmres(aifmm_h c, const double* b, double* x, double rtol, int maxit, int restart,
+                         int use_precond, int* iters, double* relres) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  if (!h.built || (use_precond && !h.factored)) {
+    h.err = use_precond ? "gmres with the preconditioner before factor" : "gmres before build";
+    return AIFMM_ERR_STATE;
+  }
+  if (!b || !x || !(rtol >= 0.0) || maxit < 1 || restart < 1 || restart > 512) {
+    h.err = "invalid argument (rtol >= 0, maxit >= 1, 1 <= restart <= 512)";
+    return AIFMM_ERR_INVALID;
+  }
+  Timer tm(h.stream);
+  bool xdev = is_device_ptr(x);
+  double* bin = (double*)hscratch(h, 93, sizeof(double) * h.N);
+  double* xout = xdev ? x : (double*)hscratch(h, 94, sizeof(double) * h.N);
+  if (!bin || !xout) return AIFMM_ERR_OOM;
+  int e = stage_in(h, b, bin, 1, h.N);
+  if (!e) e = run_gmres(h, bin, xout, rtol, maxit, restart, use_precond ? 1 : 0, iters, relres);
+  if ((!e || e == HNOCONV) && !xdev) {
+    if (cudaMemcpyAsync(x, xout, sizeof(double) * h.N, cudaMemcpyDeviceToHost, h.stream) != cudaSuccess) e = HCUDA;
+  }
+  if (cudaStreamSynchronize(h.stream) != cudaSuccess && !e) e = HCUDA;
+  h.ms_solve = tm.stop();
+  if (e == HNOCONV) h.err = "gmres: relative residual above rtol after maxit iterations";
+  if (!e || e == HNOCONV) {
+    int de = check_derr(h);
+    if (de) {
+      h.err = "gmres: device error " + std::to_string(de);
+      e = HCAPACITY;
+    }
+  }
+  return to_status(e);
 }
 
 aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {

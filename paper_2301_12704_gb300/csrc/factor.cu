@@ -1194,7 +1194,7 @@ static int factor_level(Handle& h, int l) {
     Cmp c;
     c.col = col;
     c.cnt = cnt;
-    c.eps = h.tol;
+    c.eps = h.ftol;
     c.flops = h.dacc;
     c.err = h.derr;
     c.sym = h.sym ? 1 : 0;

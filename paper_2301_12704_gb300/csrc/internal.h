@@ -60,6 +60,7 @@ struct Handle {
   int d = 2, L = 0, leaf = 0;
   KParams kp{};
   double tol = 0;
+  double ftol = 0;     // compress threshold of the factorisation
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -142,8 +143,14 @@ int run_direct_matvec(Handle& h, const double* x_dev, double* y_dev, int nrhs, i
 int run_solve_noalloc(Handle& h, double* b_dev, int nrhs, int64_t ld);
 size_t noalloc_scratch_bytes();
 
+// ---- GMRES (gmres.cu) -------------------------------------------------------
+// x = A^-1 b by restarted GMRES on the H^2 product, right-preconditioned by
+// the factorisation when prec != 0; b, x device N-vectors in original order
+int run_gmres(Handle& h, const double* b_dev, double* x_dev, double rtol, int maxit, int restart, int prec,
+              int* iters, double* relres);
+
 // error codes returned by the run_* functions (mapped to aifmm_status)
-enum HostErr { HOK = 0, HINVALID = 1, HOOM = 2, HSINGULAR = 3, HSTATE = 4, HCUDA = 6, HCAPACITY = 8 };
+enum HostErr { HOK = 0, HINVALID = 1, HOOM = 2, HSINGULAR = 3, HSTATE = 4, HNOCONV = 5, HCUDA = 6, HCAPACITY = 8 };
 
 #define AIFMM_CUDA_TRY(h, expr)                                       \
   do {                                                                \
