@@ -85,8 +85,41 @@ static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int
 // 64x64 FP64 tile: C[i0.., j0..] += alpha * A[i0.., 0..K) * B[0..K, j0..]
 // (A column-major lda, B column-major ldb, C column-major ldc), bounds
 // rows < mr, cols < nc.  256 threads, 4x4 outputs each.
+// narrow right operand (nc <= 8 columns, e.g. a single right-hand side):
+// 64 rows x 4 slices of K, one thread per (row, slice), every column of B
+// in registers; the slices are summed through shared memory
+constexpr int THIN_NC = 8;
+__device__ inline void tile_gemm_64_thin(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                         int mr, int nc, int K, double alpha) {
+  __shared__ double red[4][THIN_NC][64 + 1];
+  const int i = threadIdx.x & 63, sl = threadIdx.x >> 6;   // 256 threads
+  double acc[THIN_NC];
+#pragma unroll
+  for (int c = 0; c < THIN_NC; ++c) acc[c] = 0.0;
+  const int kq = (K + 3) / 4, ka = sl * kq, kb = min(K, ka + kq);
+  if (i < mr)
+    for (int k = ka; k < kb; ++k) {
+      double a = A[i + (size_t)k * lda];
+#pragma unroll
+      for (int c = 0; c < THIN_NC; ++c)
+        if (c < nc) acc[c] = fma(a, B[k + (size_t)c * ldb], acc[c]);
+    }
+#pragma unroll
+  for (int c = 0; c < THIN_NC; ++c) red[sl][c][i] = acc[c];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * nc; e += blockDim.x) {
+    int r = e & 63, c = e >> 6;
+    if (r < mr) C[r + (size_t)c * ldc] += alpha * (((red[0][c][r] + red[1][c][r]) + red[2][c][r]) + red[3][c][r]);
+  }
+  __syncthreads();
+}
+
 __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                     int mr, int nc, int K, double alpha) {
+  if (nc <= THIN_NC) {
+    tile_gemm_64_thin(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+    return;
+  }
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -148,6 +181,7 @@ struct SolveItem {
   int n, ld;
   double* x;
   int ldx, ncols;
+  const int* perm;   // net row permutation of ipiv (solve sweeps only), or null
 };
 
 static __global__ void __launch_bounds__(256) k_lu_solve_strip(const SolveItem* items) {
@@ -261,6 +295,83 @@ static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items,
   for (int i = 0; i < TB; ++i)
     if (i < nb) X[i] = x[i];
 }
+
+// The same diagonal-block solve for a few columns: one warp per column, the
+// 64 rows spread over the lanes (two each), x_j broadcast with a shuffle.  On
+// a part whose FP64 pipe retires a warp instruction at a fraction of the FP32
+// rate, thread-per-column with one live column would issue 2080 warp-wide FMAs
+// per column; lane-parallel rows need 128.  grid ((ncols + 3) / 4, items), 128 threads.
+template <int LOWER>
+static __global__ void __launch_bounds__(128) k_lus_diag_w(const SolveItem* items, int k0) {
+  __shared__ double T[TB][TB + 1];
+  SolveItem it = items[blockIdx.y];
+  int n = it.n;
+  if (k0 >= n) return;
+  int nb = min(TB, n - k0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int i = e % TB, j = e / TB;
+    T[i][j] = (i < nb && j < nb) ? it.a[(k0 + i) + (size_t)(k0 + j) * it.ld] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, c = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (c >= it.ncols) return;
+  double* X = it.x + (size_t)c * it.ldx + k0;
+  double x0 = lane < nb ? X[lane] : 0.0, x1 = lane + 32 < nb ? X[lane + 32] : 0.0;
+  if (LOWER) {
+    for (int j = 0; j < nb; ++j) {
+      double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      if (lane > j) x0 -= T[lane][j] * xj;
+      if (lane + 32 > j) x1 -= T[lane + 32][j] * xj;
+    }
+  } else {
+    for (int j = nb - 1; j >= 0; --j) {
+      if (j < 32) {
+        if (lane == j) x0 /= T[j][j];
+      } else if (lane == j - 32) {
+        x1 /= T[j][j];
+      }
+      double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      if (lane < j) x0 -= T[lane][j] * xj;
+      if (lane + 32 < j) x1 -= T[lane + 32][j] * xj;
+    }
+  }
+  if (lane < nb) X[lane] = x0;
+  if (lane + 32 < nb) X[lane + 32] = x1;
+}
+
+// row interchanges as one gather: X[i] := X[perm[i]] with perm the net
+// permutation of the LU's sequential interchanges; a column at a time
+// through shared memory (n doubles).  grid (column groups of 8, items)
+static __global__ void __launch_bounds__(256) k_lus_gather(const SolveItem* items) {
+  extern __shared__ double tmp[];
+  SolveItem it = items[blockIdx.y];
+  const int n = it.n;
+  if (n == 0) return;
+  const int c0 = blockIdx.x * 8, c1 = min(it.ncols, c0 + 8);
+  for (int c = c0; c < c1; ++c) {
+    double* X = it.x + (size_t)c * it.ldx;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = X[it.perm[i]];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[i] = tmp[i];
+    __syncthreads();
+  }
+}
+
+// net permutation of the sequential interchanges ipiv[0..n): perm[i] is the
+// original row that ends in row i (one thread; n integer swaps)
+__device__ inline void ipiv_to_perm(const int* ipiv, int n, int* perm) {
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int k = 0; k < n; ++k) {
+    int q = ipiv[k];
+    if (q != k) {
+      int x = perm[k];
+      perm[k] = perm[q];
+      perm[q] = x;
+    }
+  }
+}
+
+static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) { ipiv_to_perm(ipiv, n, perm); }
 
 // trailing update after diagonal block k0: lower -> rows below, upper -> rows
 // above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)

@@ -58,6 +58,7 @@ LV view(Handle& h, FacLevel& F) {
   v.Vd = F.Vd;
   v.LU = F.LU;
   v.ipiv = F.ipiv;
+  v.pperm = F.pperm;
   v.flag = F.flag;
   return v;
 }
@@ -871,7 +872,16 @@ __global__ void k_coupled(LV v, Elim e) {
   si.x = e.Z + (size_t)t * v.P * e.ncmax;
   si.ldx = v.P;
   si.ncols = co;
+  si.perm = nullptr;
   e.sv[t] = si;
+}
+
+// net row permutation of each box's pivot LU, for the solve sweeps; one thread per box
+__global__ void k_piv_perm(LV v, int col, int cnt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  int b = colour_box(col, t, v.d, v.l);
+  ipiv_to_perm(v.piv(b), v.m[b] + v.r[b], v.pp(b));
 }
 
 // Piv = [[K_bb, U_b], [V_b^T, 0]] into the LU storage; grid cnt
@@ -1034,9 +1044,10 @@ static int alloc_level(Handle& h, FacLevel& F) {
   F.Vd = hnew<double>(h, nb * F.R * std::max(1, F.Rp));
   F.LU = hnew<double>(h, nb * F.P * F.P, false);
   F.ipiv = hnew<int>(h, nb * F.P);
+  F.pperm = hnew<int>(h, nb * F.P, false);
   F.flag = hnew<unsigned>(h, nb * F.ns5);
   if (!F.m || !F.r || !F.xoff || !F.XX || !F.XY || !F.LX || !F.LY || !F.U || !F.V || !F.Ud || !F.Vd || !F.LU ||
-      !F.ipiv || !F.flag)
+      !F.ipiv || !F.pperm || !F.flag)
     return HOOM;
   F.bytes = sizeof(double) * nb *
             ((size_t)F.ns5 * (F.M * F.M + 2 * F.M * F.R) + (size_t)F.ns6 * F.R * F.R + 2 * F.M * F.R +
@@ -1305,6 +1316,7 @@ static int factor_level(Handle& h, int l) {
         k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
       }
     }
+    k_piv_perm<<<(cnt + 127) / 128, 128, 0, st>>>(v, col, cnt); ++h.nlaunch;
     dp.end();
     delete gt;
     // ---- Z = Piv^-1 B and the Schur update
@@ -1442,10 +1454,11 @@ int run_factor(Handle& h) {
   const int nt = std::max(1, h.ntop);
   h.top = hnew<double>(h, (size_t)nt * nt);
   h.top_ipiv = hnew<int>(h, nt);
+  h.top_perm = hnew<int>(h, nt, false);
   int* toff = hnew<int>(h, F2.nb + 1, false);
   double* cm = hnew<double>(h, nt);
   LuItem* it = hnew<LuItem>(h, 1, false);
-  if (!h.top || !h.top_ipiv || !toff || !cm || !it) return HOOM;
+  if (!h.top || !h.top_ipiv || !h.top_perm || !toff || !cm || !it) return HOOM;
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * (F2.nb + 1), cudaMemcpyHostToDevice, st));
   LV v2 = view(h, F2);
   k_top_assemble<<<dim3(F2.nb, F2.ns6), 256, 0, st>>>(v2, toff, h.top, h.ntop); ++h.nlaunch;
@@ -1468,6 +1481,7 @@ int run_factor(Handle& h) {
     int tiles = (h.ntop + 63) / 64;
     k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
   }
+  k_ipiv_perm<<<1, 1, 0, st>>>(h.top_ipiv, h.ntop, h.top_perm); ++h.nlaunch;
   h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));

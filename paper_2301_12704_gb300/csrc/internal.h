@@ -50,6 +50,7 @@ struct FacLevel {
   double* Vd = nullptr;  // [nb][R*Rp]  V^dag (V form, r_b x r_parent)
   double* LU = nullptr;  // [nb][P*P] LU of the pivot block, ld P
   int* ipiv = nullptr;   // [nb][P]
+  int* pperm = nullptr;  // [nb][P] net row permutation of each pivot LU
   unsigned* flag = nullptr;  // [nb][ns5] bit0: row-X ws fill-in, bit1: Lc ws fill-in
   std::vector<int> h_m, h_r;
   size_t bytes = 0;
@@ -80,6 +81,7 @@ struct Handle {
   std::vector<FacLevel> fac;
   double* top = nullptr;      // dense level-1 system LU
   int* top_ipiv = nullptr;
+  int* top_perm = nullptr;
   int ntop = 0;
   std::vector<int> top_off;   // offsets of level-2 boxes in the top system
   bool built = false, factored = false;

@@ -18,6 +18,7 @@ struct LV {
   double* Vd;
   double* LU;
   int* ipiv;
+  int* pperm;     // net row permutation of each pivot LU (ipiv applied in order)
   unsigned* flag;
 
   __host__ __device__ double* xx(int p, int s) const { return XX + ((size_t)p * ns5 + s) * M * M; }  // ld M
@@ -30,6 +31,7 @@ struct LV {
   __host__ __device__ double* vd(int p) const { return Vd + (size_t)p * R * Rp; }                    // ld R
   __host__ __device__ double* lu(int p) const { return LU + (size_t)p * P * P; }                     // ld P
   __host__ __device__ int* piv(int p) const { return ipiv + (size_t)p * P; }
+  __host__ __device__ int* pp(int p) const { return pperm + (size_t)p * P; }
   __host__ __device__ int centre5() const { return d == 2 ? 12 : 62; }
 };
 

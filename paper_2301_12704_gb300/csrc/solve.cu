@@ -38,6 +38,7 @@ LV view(Handle& h, FacLevel& F) {
   v.Vd = F.Vd;
   v.LU = F.LU;
   v.ipiv = F.ipiv;
+  v.pperm = F.pperm;
   v.flag = F.flag;
   return v;
 }
@@ -78,61 +79,54 @@ __global__ void k_leaf_out(LV v, SV s, const int* __restrict__ start, const int*
   }
 }
 
-// in-block LU solve of an n x n factor (ld lda) on X (n x nrhs, ld ldx)
-__device__ void block_lu_solve(const double* A, int lda, const int* ipiv, int n, double* X, int ldx, int nrhs) {
-  if (threadIdx.x < nrhs)
-    for (int k = 0; k < n; ++k) {
-      int p = ipiv[k];
-      if (p != k) {
-        double t = X[k + (size_t)threadIdx.x * ldx];
-        X[k + (size_t)threadIdx.x * ldx] = X[p + (size_t)threadIdx.x * ldx];
-        X[p + (size_t)threadIdx.x * ldx] = t;
-      }
-    }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    for (int e = threadIdx.x; e < (n - k - 1) * nrhs; e += blockDim.x) {
-      int i = k + 1 + e % (n - k - 1), c = e / (n - k - 1);
-      X[i + (size_t)c * ldx] -= A[i + (size_t)k * lda] * X[k + (size_t)c * ldx];
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    if (threadIdx.x < nrhs) X[k + (size_t)threadIdx.x * ldx] /= A[k + (size_t)k * lda];
-    __syncthreads();
-    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
-      int i = e % k, c = e / k;
-      X[i + (size_t)c * ldx] -= A[i + (size_t)k * lda] * X[k + (size_t)c * ldx];
-    }
-    __syncthreads();
-  }
-}
+// Each box's Piv^-1 is applied with the batched blocked LU solve of the
+// factorisation (row interchanges, unit-lower and upper 64-row diagonal
+// blocks, tiled GEMM trailing updates) over the boxes of one colour; the
+// coupling products are 64x64 register-tiled GEMMs.
 
-// forward sweep, step 1: w = Piv^-1 [beta; 0] for each box of the colour
-__global__ void __launch_bounds__(256) k_fwd_lu(LV v, SV s, int col) {
-  int b = colour_box(col, blockIdx.x, v.d, v.l);
+// forward sweep, step 1: w = P^T [beta; 0] and the solve item of each box
+__global__ void k_fwd_prep(LV v, SV s, int col, SolveItem* items) {
+  int t = blockIdx.x;
+  int b = colour_box(col, t, v.d, v.l);
   const int m = v.m[b], r = v.r[b], n = m + r;
-  if (m == 0) return;
   double* w = ws(v, s, b);
+  if (threadIdx.x == 0) {
+    SolveItem it;
+    it.a = v.lu(b);
+    it.ipiv = v.piv(b);
+    it.n = m ? n : 0;
+    it.ld = v.P;
+    it.x = w;
+    it.ldx = v.P;
+    it.ncols = s.nrhs;
+    it.perm = v.pp(b);
+    items[t] = it;
+  }
+  if (m == 0) return;
+  // the LU's row interchanges are applied here, as a gather
   const double* beta = bx(v, s, b);
+  const int* pr = v.pp(b);
   for (int e = threadIdx.x; e < n * s.nrhs; e += blockDim.x) {
     int i = e % n, k = e / n;
-    w[i + (size_t)k * v.P] = i < m ? beta[i + (size_t)k * v.M] : 0.0;
+    int src = pr[i];
+    w[i + (size_t)k * v.P] = src < m ? beta[src + (size_t)k * v.M] : 0.0;
   }
-  __syncthreads();
-  block_lu_solve(v.lu(b), v.P, v.piv(b), n, w, v.P, s.nrhs);
 }
 
 // forward sweep, step 2: right-hand-side Schur operations on the coupled
 // rows: X_p -= K_pb w_x (p not yet eliminated), Lc_p -= P2L_pb w_x
-// (p eliminated), Lc_b += w_z.  grid (3^d, cnt)
-__global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col) {
-  int b = colour_box(col, blockIdx.y, v.d, v.l);
+// (p eliminated), Lc_b += w_z.  grid (3^d * rt, column tiles, cnt), 64-row
+// tiles of the target block
+__global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col, int rt) {
+  int t = blockIdx.z, o = blockIdx.x / rt, ti = blockIdx.x % rt;
+  int b = colour_box(col, t, v.d, v.l);
   const int m = v.m[b], r = v.r[b];
   if (m == 0) return;
+  int i0 = ti * 64, j0 = blockIdx.y * 64;
+  if (j0 >= s.nrhs) return;
   int bc[3], q[3];
   morton_coords(b, v.d, v.l, bc);
-  int oo = blockIdx.x;
+  int oo = o;
   for (int k = 0; k < 3; ++k) q[k] = bc[k];
   for (int k = 0; k < v.d; ++k) {
     q[k] = bc[k] + (oo % 3) - 1;
@@ -141,39 +135,38 @@ __global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col) {
   if (!in_grid(q, v.d, v.n)) return;
   int p = morton_key(q, v.d, v.l);
   const double* w = ws(v, s, b);
+  const int nc = min(64, s.nrhs - j0);
   if (p == b) {
-    double* t = bl(v, s, b);
-    for (int e = threadIdx.x; e < r * s.nrhs; e += blockDim.x) {
-      int i = e % r, k = e / r;
-      t[i + (size_t)k * v.R] += w[m + i + (size_t)k * v.P];
+    if (i0 >= r) return;
+    double* tb = bl(v, s, b);
+    int mr = min(64, r - i0);
+    for (int e = threadIdx.x; e < mr * nc; e += blockDim.x) {
+      int i = i0 + e % mr, k = j0 + e / mr;
+      tb[i + (size_t)k * v.R] += w[m + i + (size_t)k * v.P];
     }
     return;
   }
   bool elim = colour_of(q, v.d) < col;
   int sp = slot5(q, bc, v.d);
   const double* A;
-  int lda, rows;
-  double* t;
-  int ldt;
+  int lda, rows, ldt;
+  double* tp;
   if (elim) {
     A = v.lx(p, sp);
     lda = v.R;
     rows = v.r[p];
-    t = bl(v, s, p);
+    tp = bl(v, s, p);
     ldt = v.R;
   } else {
     A = v.xx(p, sp);
     lda = v.M;
     rows = v.m[p];
-    t = bx(v, s, p);
+    tp = bx(v, s, p);
     ldt = v.M;
   }
-  for (int e = threadIdx.x; e < rows * s.nrhs; e += blockDim.x) {
-    int i = e % rows, k = e / rows;
-    double acc = 0.0;
-    for (int j = 0; j < m; ++j) acc += A[i + (size_t)j * lda] * w[j + (size_t)k * v.P];
-    t[i + (size_t)k * ldt] -= acc;
-  }
+  if (i0 >= rows) return;
+  tile_gemm_64(A + i0, lda, w + (size_t)j0 * v.P, v.P, tp + i0 + (size_t)j0 * ldt, ldt, min(64, rows - i0), nc, m,
+               -1.0);
 }
 
 // level transition of the right-hand side: X rows of parent P are the Lc
@@ -193,8 +186,23 @@ __global__ void k_rhs_up(LV vc, SV sc, LV vp, SV sp, const int* __restrict__ cxo
   }
 }
 
-__global__ void k_top_in(LV v, SV s, const int* __restrict__ toff, double* __restrict__ y, int ntop) {
+// level-2 multipole right-hand sides into the dense top vector; block 0 also
+// writes the top system's solve item
+__global__ void k_top_in(LV v, SV s, const int* __restrict__ toff, double* __restrict__ y, int ntop,
+                         const double* top, const int* top_ipiv, const int* top_perm, SolveItem* item) {
   int b = blockIdx.x;
+  if (b == 0 && threadIdx.x == 0) {
+    SolveItem it;
+    it.a = top;
+    it.ipiv = top_ipiv;
+    it.n = ntop;
+    it.ld = ntop;
+    it.x = y;
+    it.ldx = ntop;
+    it.ncols = s.nrhs;
+    it.perm = top_perm;
+    *item = it;
+  }
   int r = v.r[b], o = toff[b];
   for (int e = threadIdx.x; e < r * s.nrhs; e += blockDim.x) {
     int i = e % r, k = e / r;
@@ -214,27 +222,57 @@ struct YSrc {
   int d;
 };
 
-__device__ inline double yval(const YSrc& y, int l, int q, int i, int k, int nrhs) {
-  if (l == 2) return y.top[y.toff[q] + i + (size_t)k * y.ntop];
-  int P = q >> y.d;
-  return y.px[(size_t)P * y.pM * nrhs + y.xoff[q] + i + (size_t)k * y.pM];
+// y_q as a column-major block: first entry and leading dimension
+__device__ inline const double* ybase(const YSrc& y, int l, int q, int nrhs, int& ld) {
+  if (l == 2) {
+    ld = y.ntop;
+    return y.top + y.toff[q];
+  }
+  ld = y.pM;
+  return y.px + (size_t)(q >> y.d) * y.pM * nrhs + y.xoff[q];
 }
 
-// back substitution for the boxes of a colour: [x_b; z_b] = Piv^-1
-// [beta_b - sum K_bq x_q - sum M2P_br y_r ; y_b]
-__global__ void __launch_bounds__(256) k_bwd(LV v, SV s, int col, YSrc y) {
-  int b = colour_box(col, blockIdx.x, v.d, v.l);
+// back substitution, step 1: w = [beta_b; y_b] and the solve item
+__global__ void k_bwd_prep(LV v, SV s, int col, YSrc y, SolveItem* items) {
+  int t = blockIdx.x;
+  int b = colour_box(col, t, v.d, v.l);
   const int m = v.m[b], r = v.r[b], n = m + r;
-  if (m == 0) return;
-  int bc[3], q[3];
-  morton_coords(b, v.d, v.l, bc);
   double* w = ws(v, s, b);
+  if (threadIdx.x == 0) {
+    SolveItem it;
+    it.a = v.lu(b);
+    it.ipiv = v.piv(b);
+    it.n = m ? n : 0;
+    it.ld = v.P;
+    it.x = w;
+    it.ldx = v.P;
+    it.ncols = s.nrhs;
+    it.perm = v.pp(b);
+    items[t] = it;
+  }
+  if (m == 0) return;
+  int ldy;
+  const double* yb = ybase(y, v.l, b, s.nrhs, ldy);
   const double* beta = bx(v, s, b);
   for (int e = threadIdx.x; e < n * s.nrhs; e += blockDim.x) {
     int i = e % n, k = e / n;
-    w[i + (size_t)k * v.P] = i < m ? beta[i + (size_t)k * v.M] : yval(y, v.l, b, i - m, k, s.nrhs);
+    w[i + (size_t)k * v.P] = i < m ? beta[i + (size_t)k * v.M] : yb[(i - m) + (size_t)k * ldy];
   }
-  __syncthreads();
+}
+
+// back substitution, step 2: w_x -= sum_q K_bq x_q + sum_r M2P_br y_r over the
+// neighbours; grid (row tiles, column tiles, cnt), the neighbours summed in
+// order inside each tile
+__global__ void __launch_bounds__(256) k_bwd_gemm(LV v, SV s, int col, YSrc y) {
+  int t = blockIdx.z;
+  int b = colour_box(col, t, v.d, v.l);
+  const int m = v.m[b];
+  int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  if (i0 >= m || j0 >= s.nrhs) return;
+  const int mr = min(64, m - i0), nc = min(64, s.nrhs - j0);
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  double* w = ws(v, s, b);
   int n3 = ipow(3, v.d);
   for (int o = 0; o < n3; ++o) {
     int oo = o;
@@ -249,28 +287,30 @@ __global__ void __launch_bounds__(256) k_bwd(LV v, SV s, int col, YSrc y) {
     int sq = slot5(bc, q, v.d);
     bool elim = colour_of(q, v.d) < col;
     int cols = elim ? v.r[p] : v.m[p];
+    if (cols == 0) continue;
     const double* A = elim ? v.xy(b, sq) : v.xx(b, sq);
-    for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
-      int i = e % m, k = e / m;
-      double acc = 0.0;
-      if (elim)
-        for (int j = 0; j < cols; ++j) acc += A[i + (size_t)j * v.M] * yval(y, v.l, p, j, k, s.nrhs);
-      else
-        for (int j = 0; j < cols; ++j) acc += A[i + (size_t)j * v.M] * xx_(v, s, p)[j + (size_t)k * v.M];
-      w[i + (size_t)k * v.P] -= acc;
+    int ldb;
+    const double* B;
+    if (elim) {
+      B = ybase(y, v.l, p, s.nrhs, ldb);
+    } else {
+      B = xx_(v, s, p);
+      ldb = v.M;
     }
-    __syncthreads();
+    tile_gemm_64(A + i0, v.M, B + (size_t)j0 * ldb, ldb, w + i0 + (size_t)j0 * v.P, v.P, mr, nc, cols, -1.0);
   }
-  block_lu_solve(v.lu(b), v.P, v.piv(b), n, w, v.P, s.nrhs);
+}
+
+// back substitution, step 3: x_b = w_x
+__global__ void k_bwd_out(LV v, SV s, int col) {
+  int b = colour_box(col, blockIdx.x, v.d, v.l);
+  const int m = v.m[b];
+  const double* w = ws(v, s, b);
   double* xo = xx_(v, s, b);
   for (int e = threadIdx.x; e < m * s.nrhs; e += blockDim.x) {
     int i = e % m, k = e / m;
     xo[i + (size_t)k * v.M] = w[i + (size_t)k * v.P];
   }
-}
-
-__global__ void k_top_solve(const double* A, const int* ipiv, int n, double* X, int nrhs) {
-  block_lu_solve(A, n, ipiv, n, X, n, nrhs);
 }
 
 // ---------------------------------------------------------------- H^2 product
@@ -403,23 +443,66 @@ __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ x, do
 
 }  // namespace
 
-int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
+// Piv^-1 on the solve items of one colour (or the single top item): the
+// blocked LU solve sequence of the factorisation
+// swap: 0 = interchanges already applied, 1 = gather through shared memory
+// (columns of up to MAX_GATHER rows), 2 = sequential interchanges
+constexpr int MAX_GATHER = 27 * 1024;   // rows; 216 KB of shared memory
+static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int ncols, int swap, cudaStream_t st) {
+  const int ctiles = (ncols + 63) / 64, cstr = (ncols + 127) / 128, wstr = (ncols + 3) / 4;
+  const bool narrow = ncols <= 64;
+  if (swap == 1 && P > MAX_GATHER) swap = 2;
+  if (swap == 1) {
+    k_lus_gather<<<dim3((ncols + 7) / 8, cnt), 256, sizeof(double) * (size_t)P, st>>>(items); ++h.nlaunch;
+  } else if (swap == 2) {
+    k_lus_swap<<<dim3(cstr, cnt), 128, 0, st>>>(items); ++h.nlaunch;
+  }
+  for (int k0 = 0; k0 < P; k0 += TB) {
+    if (narrow) {
+      k_lus_diag_w<1><<<dim3(wstr, cnt), 128, 0, st>>>(items, k0);
+    } else {
+      k_lus_diag<1><<<dim3(cstr, cnt), 128, 0, st>>>(items, k0);
+    }
+    ++h.nlaunch;
+    if (k0 + TB < P) {
+      k_lus_update<1><<<dim3(ctiles, (P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(items, k0); ++h.nlaunch;
+    }
+  }
+  for (int k0 = ((P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
+    if (narrow) {
+      k_lus_diag_w<0><<<dim3(wstr, cnt), 128, 0, st>>>(items, k0);
+    } else {
+      k_lus_diag<0><<<dim3(cstr, cnt), 128, 0, st>>>(items, k0);
+    }
+    ++h.nlaunch;
+    if (k0 > 0) {
+      k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(items, k0); ++h.nlaunch;
+    }
+  }
+}
+
+// the solve vectors of one call (device memory owned by the caller)
+struct SolveBufs {
+  SV sv[32];
+  double* ytop;
+  int* toff;
+  SolveItem* items;   // max boxes of a colour + 1
+};
+
+// number of solve items needed: the largest colour of any level, plus the top
+static size_t solve_items(const Handle& h) {
+  size_t mx = 1;
+  for (int l = 2; l <= h.L; ++l) mx = std::max(mx, (size_t)h.fac[l].nb);
+  return mx + 1;
+}
+
+// forward sweep (RHS Schur operations in elimination order), top solve,
+// back substitution in reverse order; b in original order, in place
+static int sweeps(Handle& h, SolveBufs& B, double* b, int nrhs, int64_t ld) {
   const int L = h.L, d = h.d;
   cudaStream_t st = h.stream;
-  std::vector<SV> sv(L + 1);
-  for (int l = L; l >= 2; --l) {
-    FacLevel& F = h.fac[l];
-    size_t nb = F.nb;
-    sv[l].nrhs = nrhs;
-    sv[l].bX = (double*)hscratch(h, 100 + 4 * l, sizeof(double) * nb * F.M * nrhs);
-    sv[l].bL = (double*)hscratch(h, 101 + 4 * l, sizeof(double) * nb * F.R * nrhs);
-    sv[l].xX = (double*)hscratch(h, 102 + 4 * l, sizeof(double) * nb * F.M * nrhs);
-    sv[l].w = (double*)hscratch(h, 103 + 4 * l, sizeof(double) * nb * F.P * nrhs);
-    if (!sv[l].bX || !sv[l].bL || !sv[l].xX || !sv[l].w) return HOOM;
-    AIFMM_CUDA_TRY(h, cudaMemsetAsync(sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
-  }
-  const int ncol = ipow(3, d);
-  // ---- forward sweep
+  SV* sv = B.sv;
+  const int ncol = ipow(3, d), ct = (nrhs + 63) / 64;
   {
     LV v = view(h, h.fac[L]);
     k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
@@ -427,11 +510,13 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
   for (int l = L; l >= 2; --l) {
     FacLevel& F = h.fac[l];
     LV v = view(h, F);
+    const int rt = (std::max(F.M, F.R) + 63) / 64;
     for (int col = 0; col < ncol; ++col) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
-      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
-      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
+      k_fwd_prep<<<cnt, 256, 0, st>>>(v, sv[l], col, B.items); ++h.nlaunch;
+      lus_apply(h, B.items, cnt, F.P, nrhs, 0, st);
+      k_fwd_upd<<<dim3(ncol * rt, ct, cnt), 256, 0, st>>>(v, sv[l], col, rt); ++h.nlaunch;
     }
     if (l > 2) {
       FacLevel& Fp = h.fac[l - 1];
@@ -440,38 +525,35 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
     }
   }
   // ---- top
-  const int nt = std::max(1, h.ntop);
-  double* ytop = (double*)hscratch(h, 99, sizeof(double) * (size_t)nt * nrhs);
-  int* toff = (int*)hscratch(h, 98, sizeof(int) * (h.top_off.size()));
-  if (!ytop || !toff) return HOOM;
-  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice, st));
+  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(B.toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice,
+                                    st));
   {
     LV v2 = view(h, h.fac[2]);
-    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop); ++h.nlaunch;
-    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs); ++h.nlaunch;
+    SolveItem* top = B.items + (solve_items(h) - 1);
+    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], B.toff, B.ytop, h.ntop, h.top, h.top_ipiv, h.top_perm, top);
+    ++h.nlaunch;
+    if (h.ntop > 0) lus_apply(h, top, 1, h.ntop, nrhs, 1, st);
   }
   // ---- back substitution, levels 2..L, colours in reverse
   for (int l = 2; l <= L; ++l) {
     FacLevel& F = h.fac[l];
     LV v = view(h, F);
     YSrc y;
-    y.top = ytop;
+    y.top = B.ytop;
     y.ntop = h.ntop;
-    y.toff = toff;
+    y.toff = B.toff;
     y.d = d;
-    if (l > 2) {
-      y.px = sv[l - 1].xX;
-      y.pM = h.fac[l - 1].M;
-      y.xoff = F.xoff;
-    } else {
-      y.px = nullptr;
-      y.pM = 0;
-      y.xoff = F.xoff;
-    }
+    y.px = l > 2 ? sv[l - 1].xX : nullptr;
+    y.pM = l > 2 ? h.fac[l - 1].M : 0;
+    y.xoff = F.xoff;
+    const int mt = (F.M + 63) / 64;
     for (int col = ncol - 1; col >= 0; --col) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
-      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
+      k_bwd_prep<<<cnt, 256, 0, st>>>(v, sv[l], col, y, B.items); ++h.nlaunch;
+      k_bwd_gemm<<<dim3(mt, ct, cnt), 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
+      lus_apply(h, B.items, cnt, F.P, nrhs, 1, st);
+      k_bwd_out<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
     }
   }
   {
@@ -480,6 +562,43 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
   }
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   return HOK;
+}
+
+// the gather's shared-memory limit, raised once per device
+static int solve_attrs(Handle& h) {
+  static bool done[64] = {};
+  const int dv = (h.device >= 0 && h.device < 64) ? h.device : 0;
+  if (!done[dv]) {
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * MAX_GATHER)));
+    done[dv] = true;
+  }
+  return HOK;
+}
+
+int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
+  const int L = h.L;
+  cudaStream_t st = h.stream;
+  if (int e = solve_attrs(h)) return e;
+  if (L + 1 > 32) return HCAPACITY;
+  SolveBufs B;
+  for (int l = L; l >= 2; --l) {
+    FacLevel& F = h.fac[l];
+    size_t nb = F.nb;
+    B.sv[l].nrhs = nrhs;
+    B.sv[l].bX = (double*)hscratch(h, 100 + 4 * l, sizeof(double) * nb * F.M * nrhs);
+    B.sv[l].bL = (double*)hscratch(h, 101 + 4 * l, sizeof(double) * nb * F.R * nrhs);
+    B.sv[l].xX = (double*)hscratch(h, 102 + 4 * l, sizeof(double) * nb * F.M * nrhs);
+    B.sv[l].w = (double*)hscratch(h, 103 + 4 * l, sizeof(double) * nb * F.P * nrhs);
+    if (!B.sv[l].bX || !B.sv[l].bL || !B.sv[l].xX || !B.sv[l].w) return HOOM;
+    AIFMM_CUDA_TRY(h, cudaMemsetAsync(B.sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
+  }
+  const int nt = std::max(1, h.ntop);
+  B.ytop = (double*)hscratch(h, 99, sizeof(double) * (size_t)nt * nrhs);
+  B.toff = (int*)hscratch(h, 98, sizeof(int) * (h.top_off.size()));
+  B.items = (SolveItem*)hscratch(h, 97, sizeof(SolveItem) * solve_items(h));
+  if (!B.ytop || !B.toff || !B.items) return HOOM;
+  return sweeps(h, B, b, nrhs, ld);
 }
 
 int run_h2_matvec(Handle& h, const double* x, double* y, int nrhs, int64_t ld) {
@@ -577,99 +696,55 @@ static int noalloc_scratch(Handle& h, double** out) {
 }
 
 int run_solve_noalloc(Handle& h, double* b, int nrhs, int64_t ld) {
-  const int L = h.L, d = h.d;
+  const int L = h.L;
   cudaStream_t st = h.stream;
+  if (int e = solve_attrs(h)) return e;
   double* base = nullptr;
   int e = noalloc_scratch(h, &base);
   if (e) return e;
   // carve the per-level vectors (256-byte aligned pieces)
   auto round = [](size_t n) { return (n + 31) & ~(size_t)31; };
+  const int nt = std::max(1, h.ntop);
+  const size_t nitem = round((solve_items(h) * sizeof(SolveItem) + sizeof(double) - 1) / sizeof(double));
   size_t need = 0;
   for (int l = L; l >= 2; --l) {
     FacLevel& F = h.fac[l];
     size_t nb = F.nb;
     need += round(nb * F.M * nrhs) * 2 + round(nb * F.R * nrhs) + round(nb * F.P * nrhs);
   }
-  const int nt = std::max(1, h.ntop);
-  need += round((size_t)nt * nrhs) + round(h.top_off.size());
+  need += round((size_t)nt * nrhs) + round(h.top_off.size()) + nitem;
   if (need > NOALLOC_SCRATCH_DOUBLES) {
     h.err = "aifmm_solve_noalloc: this problem needs " + std::to_string(need * sizeof(double)) +
             " bytes of solve vectors for nrhs=" + std::to_string(nrhs) + "; the static scratch holds " +
             std::to_string(NOALLOC_SCRATCH_DOUBLES * sizeof(double)) + " bytes";
     return HCAPACITY;
   }
-  if (L + 1 > 16) {
-    h.err = "aifmm_solve_noalloc: tree deeper than 15 levels";
+  if (L + 1 > 32) {
+    h.err = "aifmm_solve_noalloc: tree deeper than 31 levels";
     return HCAPACITY;
   }
-  SV sv[16];
+  SolveBufs B;
   size_t off = 0;
   for (int l = L; l >= 2; --l) {
     FacLevel& F = h.fac[l];
     size_t nb = F.nb;
-    sv[l].nrhs = nrhs;
-    sv[l].bX = base + off;
+    B.sv[l].nrhs = nrhs;
+    B.sv[l].bX = base + off;
     off += round(nb * F.M * nrhs);
-    sv[l].bL = base + off;
+    B.sv[l].bL = base + off;
     off += round(nb * F.R * nrhs);
-    sv[l].xX = base + off;
+    B.sv[l].xX = base + off;
     off += round(nb * F.M * nrhs);
-    sv[l].w = base + off;
+    B.sv[l].w = base + off;
     off += round(nb * F.P * nrhs);
-    AIFMM_CUDA_TRY(h, cudaMemsetAsync(sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
+    AIFMM_CUDA_TRY(h, cudaMemsetAsync(B.sv[l].bL, 0, sizeof(double) * nb * F.R * nrhs, st));
   }
-  double* ytop = base + off;
+  B.ytop = base + off;
   off += round((size_t)nt * nrhs);
-  int* toff = reinterpret_cast<int*>(base + off);
-  AIFMM_CUDA_TRY(h, cudaMemcpyAsync(toff, h.top_off.data(), sizeof(int) * h.top_off.size(), cudaMemcpyHostToDevice, st));
-  const int ncol = ipow(3, d);
-  {
-    LV v = view(h, h.fac[L]);
-    k_leaf_in<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
-  }
-  for (int l = L; l >= 2; --l) {
-    FacLevel& F = h.fac[l];
-    LV v = view(h, F);
-    for (int col = 0; col < ncol; ++col) {
-      int cnt = colour_count(col, d, F.n);
-      if (!cnt) continue;
-      k_fwd_lu<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
-      k_fwd_upd<<<dim3(ncol, cnt), 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
-    }
-    if (l > 2) {
-      FacLevel& Fp = h.fac[l - 1];
-      LV vp = view(h, Fp);
-      k_rhs_up<<<Fp.nb, 256, 0, st>>>(v, sv[l], vp, sv[l - 1], F.xoff); ++h.nlaunch;
-    }
-  }
-  {
-    LV v2 = view(h, h.fac[2]);
-    k_top_in<<<v2.nb, 256, 0, st>>>(v2, sv[2], toff, ytop, h.ntop); ++h.nlaunch;
-    k_top_solve<<<1, 256, 0, st>>>(h.top, h.top_ipiv, h.ntop, ytop, nrhs); ++h.nlaunch;
-  }
-  for (int l = 2; l <= L; ++l) {
-    FacLevel& F = h.fac[l];
-    LV v = view(h, F);
-    YSrc y;
-    y.top = ytop;
-    y.ntop = h.ntop;
-    y.toff = toff;
-    y.d = d;
-    y.px = l > 2 ? sv[l - 1].xX : nullptr;
-    y.pM = l > 2 ? h.fac[l - 1].M : 0;
-    y.xoff = F.xoff;
-    for (int col = ncol - 1; col >= 0; --col) {
-      int cnt = colour_count(col, d, F.n);
-      if (!cnt) continue;
-      k_bwd<<<cnt, 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
-    }
-  }
-  {
-    LV v = view(h, h.fac[L]);
-    k_leaf_out<<<v.nb, 256, 0, st>>>(v, sv[L], h.start + h.soff[L], h.perm, b, ld); ++h.nlaunch;
-  }
-  AIFMM_CUDA_TRY(h, cudaGetLastError());
-  return HOK;
+  B.toff = reinterpret_cast<int*>(base + off);
+  off += round(h.top_off.size());
+  B.items = reinterpret_cast<SolveItem*>(base + off);
+  return sweeps(h, B, b, nrhs, ld);
 }
 
 }  // namespace aifmm
