@@ -64,27 +64,34 @@ static __global__ void __launch_bounds__(256) k_lu_panel(const LuItem* items, in
   }
 }
 
-// U12 = L11^-1 A12 for the columns right of the panel; grid (colchunks, items)
+// U12 = L11^-1 A12 for the columns right of the panel: one warp per column,
+// lane i holding row k0 + i, x_j broadcast with a shuffle (lane-dense FP64;
+// see k_lus_diag_w).  grid (column groups of 4, items), 128 threads
 static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int k0) {
+  __shared__ double L[LU_NB][LU_NB + 1];
   LuItem it = items[blockIdx.y];
   int n = it.n;
-  int kend = min(n, k0 + LU_NB);
-  int c = kend + blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n || c >= n) return;
+  if (k0 >= n) return;
+  int kend = min(n, k0 + LU_NB), nb = kend - k0;
   double* A = it.a;
   const int ld = it.ld;
-  double x[LU_NB];
-  for (int j = k0; j < kend; ++j) x[j - k0] = A[j + (size_t)c * ld];
-  for (int j = k0; j < kend; ++j) {
-    double xj = x[j - k0];
-    for (int i = j + 1; i < kend; ++i) x[i - k0] -= A[i + (size_t)j * ld] * xj;
+  for (int e = threadIdx.x; e < LU_NB * LU_NB; e += blockDim.x) {
+    int i = e % LU_NB, j = e / LU_NB;
+    L[i][j] = (i < nb && j < nb) ? A[(k0 + i) + (size_t)(k0 + j) * ld] : 0.0;
   }
-  for (int j = k0; j < kend; ++j) A[j + (size_t)c * ld] = x[j - k0];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  int c = kend + blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (c >= n) return;
+  double* X = A + (size_t)c * ld + k0;
+  double x = lane < nb ? X[lane] : 0.0;
+  for (int j = 0; j < nb; ++j) {
+    double xj = __shfl_sync(0xffffffffu, x, j);
+    if (lane > j) x -= L[lane][j] * xj;
+  }
+  if (lane < nb) X[lane] = x;
 }
 
-// 64x64 FP64 tile: C[i0.., j0..] += alpha * A[i0.., 0..K) * B[0..K, j0..]
-// (A column-major lda, B column-major ldb, C column-major ldc), bounds
-// rows < mr, cols < nc.  256 threads, 4x4 outputs each.
 // narrow right operand (nc <= 8 columns, e.g. a single right-hand side):
 // 64 rows x 4 slices of K, one thread per (row, slice), every column of B
 // in registers; the slices are summed through shared memory
@@ -114,6 +121,10 @@ __device__ inline void tile_gemm_64_thin(const double* A, int lda, const double*
   __syncthreads();
 }
 
+// 64x64 FP64 tile: C[i0.., j0..] += alpha * A[i0.., 0..K) * B[0..K, j0..]
+// (A column-major lda, B column-major ldb, C column-major ldc), bounds
+// rows < mr, cols < nc.  256 threads, 4x4 outputs each (the thin form above
+// when nc <= THIN_NC).
 __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                     int mr, int nc, int K, double alpha) {
   if (nc <= THIN_NC) {
@@ -338,6 +349,13 @@ static __global__ void __launch_bounds__(128) k_lus_diag_w(const SolveItem* item
   if (lane < nb) X[lane] = x0;
   if (lane + 32 < nb) X[lane + 32] = x1;
 }
+
+// Which diagonal-block form to launch for `cols` columns in total: one
+// thread per column issues 2080 FP64 warp instructions per 32 columns, one
+// warp per column 128 per column; with at most one warp per SM sub-partition
+// (152 x 4) each form takes max(1, cols / (32 * 608)) resp. cols / 608 rounds,
+// so the warp form wins below 608 * 2080 / 128 = 9880 columns.
+inline bool lus_warp_diag(int items, int ncols) { return (long long)items * ncols < 9880; }
 
 // row interchanges as one gather: X[i] := X[perm[i]] with perm the net
 // permutation of the LU's sequential interchanges; a column at a time

@@ -902,7 +902,9 @@ __global__ void k_piv_build(LV v, Elim e) {
   }
 }
 
-// B = A[pivot rows, coupled columns]: [c_C; 0] for x_q / y_q, [0; -I] for y_b
+// B = A[pivot rows, coupled columns]: [c_C; 0] for x_q / y_q, [0; -I] for y_b,
+// stored with the pivot LU's row interchanges already applied (row i of Z
+// holds row pp[i] of B)
 __global__ void k_z_build(LV v, Elim e) {
   int t = blockIdx.y, ci = blockIdx.x;
   if (ci >= e.ncol[t]) return;
@@ -912,10 +914,11 @@ __global__ void k_z_build(LV v, Elim e) {
   const int m = v.m[b], r = v.r[b], n = m + r, P = v.P;
   Coupled C = e.cols[(size_t)t * MAXC + ci];
   double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)C.off * P;
+  const int* pr = v.pp(b);
   if (C.type == 2) {
     for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
       int i = x % n, j = x / n;
-      Z[i + (size_t)j * P] = (i - m == j) ? -1.0 : 0.0;
+      Z[i + (size_t)j * P] = (pr[i] - m == j) ? -1.0 : 0.0;
     }
     return;
   }
@@ -924,7 +927,8 @@ __global__ void k_z_build(LV v, Elim e) {
   const double* src = C.type == 0 ? v.xx(b, s) : v.xy(b, s);
   for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
     int i = x % n, j = x / n;
-    Z[i + (size_t)j * P] = i < m ? src[i + (size_t)j * v.M] : 0.0;
+    int r = pr[i];
+    Z[i + (size_t)j * P] = r < m ? src[r + (size_t)j * v.M] : 0.0;
   }
 }
 
@@ -1311,7 +1315,7 @@ static int factor_level(Handle& h, int l) {
           k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
         }
         k_lu_laswp<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
-        k_lu_trsm<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
+        k_lu_trsm<<<dim3((F.P + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
         int tiles = (F.P + 63) / 64;
         k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
       }
@@ -1325,19 +1329,31 @@ static int factor_level(Handle& h, int l) {
     k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e); ++h.nlaunch;
     dp.end();
     {
-      // blocked LU solve of Z: interchanges, unit-lower blocks downwards,
-      // upper blocks upwards, each trailing update a tiled GEMM
+      // blocked LU solve of Z (interchanges applied by k_z_build): unit-lower
+      // blocks downwards, upper blocks upwards, each diagonal block one warp
+      // per column, each trailing update a tiled GEMM
       dp.begin("lus");
-      const int ctiles = (e.ncmax + 63) / 64, cstr = (e.ncmax + 127) / 128;
-      k_lus_swap<<<dim3(cstr, cnt), 128, 0, st>>>(e.sv); ++h.nlaunch;
+      const int ctiles = (e.ncmax + 63) / 64;
+      const int wstr = (e.ncmax + 3) / 4, cstr = (e.ncmax + 127) / 128;
+      const bool wdiag = lus_warp_diag(cnt, e.ncmax);
       for (int k0 = 0; k0 < F.P; k0 += TB) {
-        k_lus_diag<1><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        if (wdiag) {
+          k_lus_diag_w<1><<<dim3(wstr, cnt), 128, 0, st>>>(e.sv, k0);
+        } else {
+          k_lus_diag<1><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0);
+        }
+        ++h.nlaunch;
         if (k0 + TB < F.P) {
           k_lus_update<1><<<dim3(ctiles, (F.P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
         }
       }
       for (int k0 = ((F.P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
-        k_lus_diag<0><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0); ++h.nlaunch;
+        if (wdiag) {
+          k_lus_diag_w<0><<<dim3(wstr, cnt), 128, 0, st>>>(e.sv, k0);
+        } else {
+          k_lus_diag<0><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0);
+        }
+        ++h.nlaunch;
         if (k0 > 0) {
           k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
         }
@@ -1477,7 +1493,7 @@ int run_factor(Handle& h) {
       k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
     }
     k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
-    k_lu_trsm<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
+    k_lu_trsm<<<dim3((h.ntop + 3) / 4, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
     k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
   }

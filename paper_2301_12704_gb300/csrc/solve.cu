@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ x, do
 constexpr int MAX_GATHER = 27 * 1024;   // rows; 216 KB of shared memory
 static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int ncols, int swap, cudaStream_t st) {
   const int ctiles = (ncols + 63) / 64, cstr = (ncols + 127) / 128, wstr = (ncols + 3) / 4;
-  const bool narrow = ncols <= 64;
+  const bool narrow = lus_warp_diag(cnt, ncols);
   if (swap == 1 && P > MAX_GATHER) swap = 2;
   if (swap == 1) {
     k_lus_gather<<<dim3((ncols + 7) / 8, cnt), 256, sizeof(double) * (size_t)P, st>>>(items); ++h.nlaunch;
