@@ -325,21 +325,32 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 // in order, then the largest residual column among the fill-ins while its
 // norm exceeds eps * max_j ||F_j||.  Produces Q[:, :rank] explicitly.
 // One thread-block cluster of QC CTAs per (box, side) (QC chosen per level
-// by the host so that the colour's clusters fill the GPU): CTA c updates the
-// trailing columns j with j % QC == c; the pivot is reduced across the
-// cluster through distributed shared memory; CTA 0 swaps columns and builds
-// each reflector.  Every CTA derives the loop exit from the same cluster-wide
-// values, so all of them pass the same sequence of cluster barriers.
-// With sym only side 0 is factored and its rank serves both sides.
-// grid (QC * sides * cnt), 256 threads, launched with cluster size QC.
-__global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
+// by the host so that the colour's clusters fill the GPU); CTA c owns the
+// columns j with j % QC == c and keeps their residual norms in shared memory.
+// Columns are never swapped: step k takes pivot column p, one warp of every
+// CTA builds the reflector from it (rows k..m-1) in the CTA's shared memory,
+// and each CTA applies it to its live columns, four per warp at a time; the
+// owner stores the reflector into column p one step later (every CTA has read
+// the column by then).  Residual norms are downdated (minus the square of the
+// new row-k entry) and recomputed exactly when they fall below 1e-8 of their
+// last exact value, so a norm compared with the threshold has not lost its
+// digits to cancellation.  One cluster barrier per step (two when a pivot is
+// searched: the candidates are exchanged through distributed shared memory).
+// Every CTA derives the loop exit from the same cluster-wide values, so all
+// pass the same barriers.  With sym only side 0 is factored and its rank
+// serves both sides.
+// grid (QC * sides * cnt), 256 to 1024 threads, cluster size QC; dynamic shared
+// memory: 2 M doubles (reflectors k and k-1), M ints (pivot order),
+// 2 ceil(WC / QC) doubles (own column norms and their last exact values).
+__global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int QC = (int)cl.num_blocks();
+  extern __shared__ double dyn[];
   __shared__ double shv[32];
   __shared__ int shi[32];
   __shared__ double shs[32];
-  __shared__ ArgMax lbest;
+  __shared__ ArgMax lbest[2];
   __shared__ double lmax;
   const int cr = (int)cl.block_rank();
   const int bs = blockIdx.x / QC;
@@ -349,16 +360,23 @@ __global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   const int m = v.m[b], n = c.nc[t * 2 + side], nf = c.rold[t];
   const int M = v.M;
   double* W = c.W + ((size_t)t * 2 + side) * M * c.WC;
-  double* cn = c.cn + ((size_t)t * 2 + side) * c.WC;
   double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
+  const int cw = (c.WC + QC - 1) / QC;
+  double* vbuf = dyn;                                    // [2][M]
+  int* pivs = reinterpret_cast<int*>(dyn + 2 * M);       // [M]
+  double* cnl = dyn + 2 * M + (M + 1) / 2;               // [cw] squared residual norms (-1: retired)
+  double* cref = cnl + cw;                               // [cw] value at the last exact computation
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // initial column norms of the fill-in columns and the threshold
+  const int nloc = n > cr ? (n - cr + QC - 1) / QC : 0;   // own columns j = cr + QC * jl
+  // initial residual norms of the own fill-in columns, and the threshold
   double mx = 0.0;
-  for (int j = nf + cr + QC * w; j < n; j += QC * nw) {
+  for (int jl = w; jl < nloc; jl += nw) {
+    int j = cr + QC * jl;
     double acc = 0.0;
-    for (int i = lane; i < m; i += 32) acc += W[i + (size_t)j * M] * W[i + (size_t)j * M];
+    if (j >= nf)
+      for (int i = lane; i < m; i += 32) acc += W[i + (size_t)j * M] * W[i + (size_t)j * M];
     acc = warp_sum(acc);
-    if (lane == 0) cn[j] = acc;
+    if (lane == 0) cnl[jl] = cref[jl] = acc;
     mx = fmax(mx, acc);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -376,89 +394,157 @@ __global__ void __launch_bounds__(256) k_cmp_qrcp(LV v, Cmp c) {
   const int kmax = min(m, n);
   int k = 0;
   for (; k < kmax; ++k) {
+    double* vref = vbuf + (size_t)(k & 1) * M;
+    // the owner stores reflector k-1 into its pivot column
+    if (k > 0 && pivs[k - 1] % QC == cr) {
+      const double* vp = vbuf + (size_t)((k - 1) & 1) * M;
+      for (int i = k - 1 + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)pivs[k - 1] * M] = vp[i];
+    }
+    int p = k;
     if (k >= nf) {
       ArgMax best;
       best.v = -1.0;
       best.i = -1;
-      int j0 = k + ((cr - k % QC) + QC) % QC;   // first j >= k with j % QC == cr
-      for (int j = j0 + QC * threadIdx.x; j < n; j += QC * blockDim.x) {
+      for (int jl = threadIdx.x; jl < nloc; jl += blockDim.x) {
+        int j = cr + QC * jl;
+        if (j < nf) continue;
         ArgMax x;
-        x.v = cn[j];
+        x.v = cnl[jl];
         x.i = j;
         best = amax_pick(best, x);
       }
       best = block_amax(best, shv, shi);
-      if (threadIdx.x == 0) lbest = best;
+      if (threadIdx.x == 0) lbest[k & 1] = best;
       cl.sync();
       ArgMax g;
       g.v = -1.0;
       g.i = -1;
-      for (int r = 0; r < QC; ++r) g = amax_pick(g, *cl.map_shared_rank(&lbest, r));
-      if (!(sqrt(fmax(g.v, 0.0)) > tau)) break;
-      if (cr == 0 && g.i != k) {
-        int p = g.i;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-          double x = W[i + (size_t)k * M];
-          W[i + (size_t)k * M] = W[i + (size_t)p * M];
-          W[i + (size_t)p * M] = x;
-        }
-        if (threadIdx.x == 0) {
-          double x = cn[k];
-          cn[k] = cn[p];
-          cn[p] = x;
-        }
-        __syncthreads();
-      }
+      for (int r = 0; r < QC; ++r) g = amax_pick(g, *cl.map_shared_rank(&lbest[k & 1], r));
+      if (!(g.i >= 0 && sqrt(fmax(g.v, 0.0)) > tau)) break;
+      p = g.i;
     }
-    if (cr == 0) {
-      // reflector from W[k:m, k], stored normalised in place
+    // reflector from W[k:m, p], normalised, built by warp 0
+    if (w == 0) {
       double acc = 0.0;
-      for (int i = k + threadIdx.x; i < m; i += blockDim.x) acc += W[i + (size_t)k * M] * W[i + (size_t)k * M];
-      double a2 = block_sum(acc, shs);
-      double alpha = sqrt(a2);
-      double x0 = W[k + (size_t)k * M];
-      __syncthreads();
+      for (int i = k + lane; i < m; i += 32) {
+        double x = W[i + (size_t)p * M];
+        vref[i] = x;
+        acc += x * x;
+      }
+      const double a2 = warp_sum(acc);
+      const double alpha = sqrt(a2);
+      const double x0 = __shfl_sync(0xffffffffu, lane == 0 ? vref[k] : 0.0, 0);
       if (alpha == 0.0) {
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)k * M] = 0.0;
+        for (int i = k + lane; i < m; i += 32) vref[i] = 0.0;
       } else {
-        double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
-        double nv = sqrt(a2 - x0 * x0 + v0 * v0);
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-          double x = i == k ? v0 : W[i + (size_t)k * M];
-          W[i + (size_t)k * M] = x / nv;
+        const double v0 = x0 + (x0 >= 0.0 ? alpha : -alpha);
+        const double inv = 1.0 / sqrt(a2 - x0 * x0 + v0 * v0);
+        for (int i = k + lane; i < m; i += 32) vref[i] = (i == k ? v0 : vref[i]) * inv;
+      }
+      if (lane == 0) {
+        pivs[k] = p;
+        if (p % QC == cr) cnl[p / QC] = -1.0;        // retired
+      }
+    }
+    __syncthreads();
+    // apply H_k to the own live columns, four per warp at once (the row loop
+    // outside, so the four columns' loads are independent)
+    for (int g0 = 4 * w; g0 < nloc; g0 += 4 * nw) {
+      bool live[4];
+      double* col[4];
+      bool any = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int jl = g0 + u, j = cr + QC * jl;
+        live[u] = jl < nloc && j != p && cnl[jl] >= 0.0;
+        any |= live[u];
+        col[u] = W + (size_t)(live[u] ? j : p) * M;   // column p is not written in this step
+      }
+      if (!any) continue;
+      double dt[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = k + lane; i < m; i += 32) {
+        double vi = vref[i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dt[u] += vi * col[u][i];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(0xffffffffu, dt[u], o);
+      double xk[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = k + lane; i < m; i += 32) {
+        double vi = vref[i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          double x = col[u][i] - 2.0 * dt[u] * vi;
+          if (live[u]) col[u][i] = x;
+          if (i == k) xk[u] = x;
+        }
+      }
+      // downdate the fill-in columns' norms; recompute where cancellation
+      // has eaten most of them (decided by lane 0, the holder of row k)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jl = g0 + u;
+        bool fill = live[u] && cr + QC * jl >= nf;
+        double nv = 0.0;
+        int redo = 0;
+        if (lane == 0 && fill) {
+          nv = cnl[jl] - xk[u] * xk[u];
+          redo = !(nv > 1e-8 * cref[jl]);
+        }
+        redo = __shfl_sync(0xffffffffu, redo, 0);
+        if (redo) {
+          double acc = 0.0;
+          for (int i = k + 1 + lane; i < m; i += 32) acc += col[u][i] * col[u][i];
+          acc = warp_sum(acc);
+          if (lane == 0) cnl[jl] = cref[jl] = acc;
+        } else if (lane == 0 && fill) {
+          cnl[jl] = nv;
         }
       }
     }
-    cl.sync();
-    // apply H_k to the trailing columns owned by this CTA, refresh norms
-    int j0 = (k + 1) + ((cr - (k + 1) % QC) + QC) % QC;
-      for (int j = j0 + QC * w; j < n; j += QC * nw) {
-        double dt = 0.0;
-        for (int i = k + lane; i < m; i += 32) dt += W[i + (size_t)k * M] * W[i + (size_t)j * M];
-        dt = warp_sum(dt);
-        double nn = 0.0;
-        for (int i = k + lane; i < m; i += 32) {
-          double x = W[i + (size_t)j * M] - 2.0 * dt * W[i + (size_t)k * M];
-          W[i + (size_t)j * M] = x;
-          if (i > k) nn += x * x;
-        }
-        nn = warp_sum(nn);
-        if (lane == 0) cn[j] = nn;
-      }
     cl.sync();
   }
-  cl.sync();   // no CTA leaves while another may still read its shared memory
   const int rank = k;
-  // form Q[:, :rank] = H_0 ... H_{rank-1} [e_0 .. e_{rank-1}]
-  for (int j = cr + QC * w; j < rank; j += QC * nw) {
-    double* y = Q + (size_t)j * M;
-    for (int i = lane; i < m; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+  if (rank == kmax && rank > 0 && pivs[rank - 1] % QC == cr) {   // last reflector (a break stored it already)
+    const double* vp = vbuf + (size_t)((rank - 1) & 1) * M;
+    for (int i = rank - 1 + threadIdx.x; i < m; i += blockDim.x) W[i + (size_t)pivs[rank - 1] * M] = vp[i];
+  }
+  cl.sync();   // reflectors visible; no CTA leaves while another may read its shared memory
+  // form Q[:, :rank] = H_0 ... H_{rank-1} [e_0 .. e_{rank-1}]; reflector kk is
+  // stored in column pivs[kk], rows kk..m-1; four columns per warp
+  for (int j0 = 4 * (cr + QC * w); j0 < rank; j0 += 4 * QC * nw) {
+    double* qc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int j = min(j0 + u, rank - 1);
+      qc[u] = Q + (size_t)j * M;
+      if (j0 + u < rank)
+        for (int i = lane; i < m; i += 32) qc[u][i] = (i == j) ? 1.0 : 0.0;
+    }
     __syncwarp();
-    for (int kk = min(j, rank - 1); kk >= 0; --kk) {
-      double dt = 0.0;
-      for (int i = kk + lane; i < m; i += 32) dt += W[i + (size_t)kk * M] * y[i];
-      dt = warp_sum(dt);
-      for (int i = kk + lane; i < m; i += 32) y[i] -= 2.0 * dt * W[i + (size_t)kk * M];
+    for (int kk = min(j0 + 3, rank - 1); kk >= 0; --kk) {
+      const double* vk = W + (size_t)pivs[kk] * M;
+      bool on[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) on[u] = j0 + u < rank && kk <= j0 + u;
+      double dt[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = kk + lane; i < m; i += 32) {
+        double vi = vk[i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dt[u] += vi * qc[u][i];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(0xffffffffu, dt[u], o);
+      for (int i = kk + lane; i < m; i += 32) {
+        double vi = vk[i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (on[u]) qc[u][i] -= 2.0 * dt[u] * vi;
+      }
       __syncwarp();
     }
   }
@@ -1239,8 +1325,19 @@ static int factor_level(Handle& h, int l) {
       int qc = 2;
       while (qc < 16 && qc * nsides * cnt < 2 * h.nsm) qc *= 2;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(qc * nsides * cnt);
-      cfg.blockDim = dim3(256);
+      // few clusters (top levels): wider CTAs, fewer columns per warp
+      const int ncta = qc * nsides * cnt;
+      cfg.gridDim = dim3(ncta);
+      cfg.blockDim = dim3(ncta <= h.nsm ? 1024 : ncta <= 2 * h.nsm ? 512 : 256);
+      cfg.dynamicSmemBytes = sizeof(double) * (2 * (size_t)F.M + (F.M + 1) / 2 + 2 * (size_t)((c.WC + qc - 1) / qc));
+      if (cfg.dynamicSmemBytes > (size_t)h.smem_optin) {
+        h.err = "compress: a box side needs " + std::to_string(cfg.dynamicSmemBytes) +
+                " bytes of shared memory per CTA";
+        return HCAPACITY;
+      }
+      if (cfg.dynamicSmemBytes > 48 * 1024)
+        AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)cfg.dynamicSmemBytes));
       cfg.stream = st;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1440,6 +1537,7 @@ int run_factor(Handle& h) {
     int smax = 0;
     AIFMM_CUDA_TRY(h, cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, h.device));
     h.panel_rows = (smax - 1024) / (int)(sizeof(double) * LU_NB);
+    h.smem_optin = smax - 2048;
     AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lu_panel_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * (size_t)h.panel_rows * LU_NB)));
   }

@@ -67,6 +67,7 @@ struct Handle {
   int device = 0;
   int nsm = 152;
   int panel_rows = 0;   // tallest LU panel factored in shared memory
+  int smem_optin = 48 * 1024;   // dynamic shared memory a kernel may opt in to
   size_t l2_bytes = 0;
   // tree
   double* pts = nullptr;      // SoA [d][N] in tree order
