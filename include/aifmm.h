@@ -84,6 +84,9 @@ typedef struct {
                       place of tol (the NNCA operators and aifmm_matvec keep tol);
                       a looser value gives the low-accuracy factorisation used as a
                       GMRES preconditioner (Sec. 4, Experiment 5). 0: tol */
+  int fma_gemm;    /* 0 (default): the Schur-update tile products run on the BF16
+                      tensor cores in FP64 precision (exact 7-bit integer digits,
+                      see aifmm_kernels.h); 1: on FP64 FMAs */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of

@@ -39,7 +39,7 @@ class Kernel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("no_symmetry", C.c_int), ("factor_tol", C.c_double)]
+                ("no_symmetry", C.c_int), ("factor_tol", C.c_double), ("fma_gemm", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -72,6 +72,8 @@ def lib():
         L.aifmm_direct_matvec.argtypes = [vp, vp, vp, cint, i64]
         L.aifmm_gmres.argtypes = [vp, vp, vp, dbl, cint, cint, cint, C.POINTER(cint), C.POINTER(dbl)]
         L.aifmm_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.aifmm_dgemm_tc.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
+        L.aifmm_dgemm_tc.restype = C.c_int
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
         L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
         L.aifmm_level_pivots.argtypes = [vp, cint, vp]
@@ -117,18 +119,19 @@ class Handle:
 
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
                 depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True,
-                factor_tol: float = 0.0) -> Handle:
+                factor_tol: float = 0.0, fma_gemm: bool = False) -> Handle:
     """Build tree, lists, NNCA operators and the extended system (C: aifmm_build).
 
     ``symmetric=False`` selects the general elimination (rows and columns
     compressed separately, every Schur block computed); ``factor_tol`` > 0 is
-    the compress threshold of the factorisation (default: ``tol``)."""
+    the compress threshold of the factorisation (default: ``tol``);
+    ``fma_gemm`` runs the Schur tiles on FP64 FMAs instead of the tensor cores."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
     o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
-                float(factor_tol))
+                float(factor_tol), int(bool(fma_gemm)))
     out = C.c_void_p()
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
@@ -220,6 +223,23 @@ def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: in
     if st != 0 and (st != 5 or raise_noconv):
         _check(st, h.raw)
     return x, it.value, rr.value
+
+
+def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None) -> None:
+    """C_ += alpha A B on the tensor cores in FP64 precision (C: aifmm_dgemm_tc).
+    A, B, C_ CUDA float64 tensors, column-major (e.g. ``t.t().contiguous().t()``)."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k2 == k and tuple(C_.shape) == (m, n)
+    def ld(t):
+        assert t.is_cuda and (t.stride(0) == 1 or t.shape[0] == 1), "column-major CUDA tensors"
+        return max(1, t.shape[0], t.stride(1) if t.shape[1] > 1 else 1)
+
+    st = lib().aifmm_dgemm_tc(C.c_void_p(A.data_ptr()), ld(A), C.c_void_p(B.data_ptr()), ld(B),
+                              C.c_void_p(C_.data_ptr()), ld(C_), m, n, k, float(alpha),
+                              C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise AifmmError(st, "aifmm_dgemm_tc failed")
 
 
 def torch_empty_like(t):

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaifmm.so")
-SOURCES = ["api.cu", "tree.cu", "nnca.cu", "factor.cu", "solve.cu", "gmres.cu"]
+SOURCES = ["api.cu", "tree.cu", "nnca.cu", "factor.cu", "solve.cu", "gmres.cu", "gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,6 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(CSRC, x) for x in os.listdir(CSRC) if x.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "aifmm.h"))
+    headers.append(os.path.join(HERE, "..", "include", "aifmm_kernels.h"))
     hdr_time = max(os.path.getmtime(x) for x in headers)
     exe = nvcc()
     jobs = []

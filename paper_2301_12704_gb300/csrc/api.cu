@@ -162,6 +162,7 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.kp.inv_len2 = k->kind == AIFMM_K_GAUSS ? 1.0 / (k->length * k->length) : 0.0;
   h.profile = opt && opt->profile;
   h.sym = !(opt && opt->no_symmetry);
+  h.fma_gemm = opt && opt->fma_gemm;
   if (opt && opt->stream) {
     h.stream = (cudaStream_t)opt->stream;
   } else {

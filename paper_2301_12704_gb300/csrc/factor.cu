@@ -29,6 +29,7 @@
 #include "dense.cuh"
 #include "internal.h"
 #include "level.cuh"
+#include "ozaki.cuh"
 
 namespace aifmm {
 
@@ -1037,6 +1038,9 @@ __device__ inline double* schur_target(const LV& v, int rbox, int rtype, int cty
 // elimination keeps: Piv and the Schur complement stay symmetric) the block
 // (j, i) is the transpose of (i, j): only i <= j is computed and each
 // off-diagonal tile is also stored transposed at its mirror.
+// OZ: the tile product on the tensor cores (tile_gemm_64_oz, FP64 precision,
+// OZ_SMEM bytes of dynamic shared memory) instead of FP64 FMAs.
+template <bool OZ>
 __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   int t = blockIdx.z;
   int ri = blockIdx.y / tpb, ti = blockIdx.y % tpb;
@@ -1068,7 +1072,12 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   int sp = slot5(pc, bc, v.d);
   const double* A = R.type == 0 ? v.xx(R.box, sp) : v.lx(R.box, sp);
   int lda = R.type == 0 ? v.M : v.R;
-  tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
+  if (OZ) {
+    extern __shared__ unsigned char ozs[];
+    tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
+  } else {
+    tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
+  }
   // a block between well-separated boxes is a pending fill-in unless both
   // boxes are eliminated (an M2L fill-in, kept without compression)
   const bool ws = C.type != 2 && !(R.type == 1 && C.type == 1) && cheb(pc, qc, v.d) == 2;
@@ -1461,7 +1470,12 @@ static int factor_level(Handle& h, int l) {
     int tpb = (F.M + 63) / 64;
     gt = new GroupTimer(h, Handle::G_SCHUR);
     dp.begin("schur");
-    k_schur<<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb, h.sym ? 1 : 0); ++h.nlaunch;
+    if (h.fma_gemm) {
+      k_schur<false><<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb, h.sym ? 1 : 0);
+    } else {
+      k_schur<true><<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, OZ_SMEM, st>>>(v, e, tpb, h.sym ? 1 : 0);
+    }
+    ++h.nlaunch;
     dp.end();
     delete gt;
     AIFMM_CUDA_TRY(h, cudaGetLastError());
@@ -1531,6 +1545,7 @@ int run_factor(Handle& h) {
   if (!h.dacc) h.dacc = hnew<double>(h, 4);
   if (!h.dacc) return HOOM;
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_schur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   {
     // tallest LU panel kept in shared memory: (rows x 32) doubles within the
     // opt-in limit of the device

@@ -1,0 +1,243 @@
+// FP64 matrix products on the BF16 tensor cores by exact integer slicing
+// (the splitting idea of Ozaki et al.: write each operand as a short sum of
+// small integers times powers of two, multiply the pieces exactly, add the
+// pieces' products at full precision).
+//
+// Why: GB300 retires FP64 FMAs at ~1.2 TFLOP/s but BF16 MMAs with FP32
+// accumulation two to three orders of magnitude faster, and the Schur
+// complement update of the factorisation is a dense FP64 contraction.
+//
+// One 64 x 64 output tile, K in chunks of OZ_KC:
+//  * every row of the A chunk (every column of the B chunk) is scaled by its
+//    largest binary exponent E; each entry becomes the integer
+//    a = round(|x| 2^(48 - e_E)) < 2^49 (e_E the unbiased exponent of 2^E;
+//    integer operations on the IEEE bit pattern, no FP64 instruction), cut
+//    into OZ_S = 7 digits d_0..d_6 of 7 bits (d_0 may be 128), stored as BF16
+//    values d_s 2^(-7 s) -- exact, at most 8 significant bits;
+//  * the product of digits s and t (0-based) carries the scale 2^(-7 (s+t))
+//    and is an integer below 2^14 times it.  The MMA adds its sixteen products
+//    to the FP32 accumulator keeping about 22 bits below the largest operand
+//    (measured on GB300: 2^22 + 1 -> 2^22, 2^22 + 2 kept; truncation), so the
+//    MMAs of one weight s + t <= 4 (at most 5 digit pairs) accumulated over 32
+//    of K stay below 5 * 32 * 2^14 < 2^22 and are exact; the pairs with
+//    s + t = 5..8 (weight 2^-35 and below) share one FP32 accumulator whose
+//    truncation stays near 2^-54 of the tile's scale;
+//  * every 32 of K the exact weights are summed as one 64-bit integer, the
+//    rest added in FP64, and the result scaled by 2^(E_row + E_col) into the
+//    FP64 result registers.
+// Pairs with s + t > 8 are dropped: a digit pair contributes up to 2^14 times
+// its weight, so s + t = 7, 8 still matter at the 2^-48 level while s + t >= 9
+// is below 2^-49 of the top digits' product: 39 digit-pair MMAs per 16-deep
+// step.  The result has
+// FP64-size error relative to |A| |B| rows and columns of moderate dynamic
+// range; an entry 2^-d below its row's (column's) largest in a chunk keeps
+// 49 - d bits.
+// 256 threads (8 warps, each a 32 x 16 sub-tile: 2 x 2 MMAs of m16n8k16).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace aifmm {
+
+constexpr int OZ_S = 7;                // digits per operand
+constexpr int OZ_KC = 64;              // K chunk
+constexpr int OZ_LD = OZ_KC + 8;       // padded smem row (bf16 elements): conflict-free fragment loads
+constexpr int OZ_SMEM = 2 * OZ_S * 64 * OZ_LD * 2 + 2 * 64 * 4;   // bytes of dynamic shared memory
+
+// biased exponent of |x| (0 for zero and denormals, which are flushed)
+__device__ inline int oz_bexp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// the OZ_S digits of x relative to the biased exponent E >= bexp(x): with
+// |x| = m 2^(e - 1075) (53-bit m), a = round(m 2^(e - E - 4)) = sum_s d_s 2^(42 - 7 s);
+// written as BF16 values +-d_s 2^(-7 s), so that |x| = 2^(E - 1029) sum_s value_s
+__device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride) {
+  long long bits = __double_as_longlong(x);
+  int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long a = 0;
+  if (e != 0) {
+    unsigned long long m = ((unsigned long long)bits & 0xfffffffffffffull) | (1ull << 52);
+    int sh = E - e + 4;                  // 53-bit mantissa -> 49 bits below 2^(E)
+    if (sh < 64) a = (m + (1ull << (sh - 1))) >> sh;
+  }
+  const bool neg = bits < 0;
+  float scale = 1.0f;
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    unsigned d = s == 0 ? (unsigned)(a >> 42) : (unsigned)((a >> (42 - 7 * s)) & 0x7f);
+    float v = (float)d * scale;
+    out[s * stride] = __float2bfloat16_rn(neg ? -v : v);
+    scale *= 0.0078125f;                 // 2^-7
+  }
+}
+
+__device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[0..mr, 0..nc] += alpha * A[0..mr, 0..K) B[0..K, 0..nc]; A column-major
+// (lda), B column-major (ldb), C column-major (ldc).  smem: OZ_SMEM bytes.
+__device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                       int mr, int nc, int K, double alpha, unsigned char* smem) {
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [OZ_S][64][OZ_LD]
+  __nv_bfloat16* Bs = As + OZ_S * 64 * OZ_LD;                            // [OZ_S][64][OZ_LD] (col, k)
+  int* ea = reinterpret_cast<int*>(Bs + OZ_S * 64 * OZ_LD);              // [64] row exponents
+  int* eb = ea + 64;                                                     // [64] column exponents
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wr = (w & 1) * 32, wc = (w >> 1) * 16;                       // warp sub-tile origin
+  const int g = lane >> 2, cq = lane & 3;
+  double acc64[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc64[a][b][q] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += OZ_KC) {
+    const int kc = min(OZ_KC, K - k0);
+    // ---- stage: exponents (rows of A, columns of B over this chunk)
+    if (tid < 128) (tid < 64 ? ea : eb)[tid & 63] = 0;
+    __syncthreads();
+    // A: warp w takes k = 8w..8w+7, lanes the rows lane and lane + 32
+    double av[8][2];
+    int am0 = 0, am1 = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int k = 8 * w + q;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int i = lane + 32 * h;
+        double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
+        av[q][h] = x;
+        int e = oz_bexp(x);
+        if (h == 0) am0 = max(am0, e); else am1 = max(am1, e);
+      }
+    }
+    atomicMax(&ea[lane], am0);
+    atomicMax(&ea[lane + 32], am1);
+    // B: warp w takes columns 8w..8w+7, lanes k = lane and lane + 32
+    double bv[8][2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = 8 * w + q;
+      int bm = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int k = lane + 32 * h;
+        double x = (j < nc && k < kc) ? B[(k0 + k) + (size_t)j * ldb] : 0.0;
+        bv[q][h] = x;
+        bm = max(bm, oz_bexp(x));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      if (lane == 0) eb[j] = bm;
+    }
+    __syncthreads();
+    // ---- stage: digits into shared memory
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int k = 8 * w + q;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int i = lane + 32 * h;
+        oz_digits(av[q][h], ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = 8 * w + q;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int k = lane + 32 * h;
+        oz_digits(bv[q][h], eb[j], Bs + j * OZ_LD + k, 64 * OZ_LD);
+      }
+    }
+    __syncthreads();
+    // ---- MMAs, flushed every 32 of K: digit-pair weights s + t = 0..4 each
+    // in its own accumulator (exact), 5..8 together
+    for (int kh = 0; kh < OZ_KC; kh += 32) {
+      float acc[6][2][2][4];
+#pragma unroll
+      for (int x = 0; x < 6; ++x)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[x][a][b][q] = 0.f;
+#pragma unroll
+      for (int kk = kh; kk < kh + 32; kk += 16) {
+        uint32_t bf[OZ_S][2][2];
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const __nv_bfloat16* base = Bs + t * 64 * OZ_LD + (wc + 8 * b + g) * OZ_LD + kk + 2 * cq;
+            bf[t][b][0] = *reinterpret_cast<const uint32_t*>(base);
+            bf[t][b][1] = *reinterpret_cast<const uint32_t*>(base + 8);
+          }
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) {
+          uint32_t af[2][4];
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const __nv_bfloat16* base = As + s * 64 * OZ_LD + (wr + 16 * a + g) * OZ_LD + kk + 2 * cq;
+            af[a][0] = *reinterpret_cast<const uint32_t*>(base);
+            af[a][1] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD);
+            af[a][2] = *reinterpret_cast<const uint32_t*>(base + 8);
+            af[a][3] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD + 8);
+          }
+#pragma unroll
+          for (int t = 0; t < OZ_S; ++t) {
+            if (s + t > OZ_S + 1) continue;     // s + t >= 9: below 2^-63 x 2^14, dropped
+            const int grp = min(s + t, 5);
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+              for (int b = 0; b < 2; ++b) oz_mma(acc[grp][a][b], af[a], bf[t][b]);
+          }
+        }
+      }
+      // ---- recombine: the exact weights as one 64-bit integer in units of
+      // 2^-28, the rest in FP32, then the row and column scales in FP64
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
+            long long tot = 0;
+            float wgt = 1.0f;
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+              tot += (long long)__float2int_rn(acc[x][a][b][q] * wgt) << (7 * (4 - x));
+              wgt *= 128.0f;
+            }
+            double sum = fma((double)tot, 0x1p-28, (double)acc[5][a][b][q]);
+            // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
+            int be = ea[i] + eb[j] - 2058 + 1023;
+            double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
+            acc64[a][b][q] = fma(sum, sc, acc64[a][b][q]);
+          }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
+        if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc64[a][b][q];
+      }
+}
+
+}  // namespace aifmm

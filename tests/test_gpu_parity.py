@@ -84,14 +84,16 @@ def _oracle_solution(w, pts, b):
     return _ORACLE_X[w.name]
 
 
-@pytest.mark.parametrize("symmetric", [True, False], ids=["sym", "general"])
+@pytest.mark.parametrize("symmetric,fma", [(True, False), (False, False), (True, True)],
+                         ids=["sym", "general", "sym-fp64fma"])
 @pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
-def test_factor_solve_matches_oracle(A, w, symmetric):
-    """Both elimination modes against the oracle's general elimination: the
-    symmetric mode (one RRQR per box, mirrored Schur blocks) differs from it
+def test_factor_solve_matches_oracle(A, w, symmetric, fma):
+    """Both elimination modes, and the Schur tiles on the tensor cores or on
+    FP64 FMAs, against the oracle's general elimination: they differ from it
     only by rounding and the RRQR cut-off, so the same 10 tol bound holds."""
     pts, b = W.points_and_rhs(w, nrhs=2)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, symmetric=symmetric)
+    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, symmetric=symmetric,
+                      fma_gemm=fma)
     A.aifmm_factor(h)
     x = A.aifmm_solve(h, b)
     xo, xd = _oracle_solution(w, pts, b)
