@@ -4,6 +4,7 @@
 // register-tiled GEMM tile.
 #pragma once
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace aifmm {
 
@@ -168,6 +169,20 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
       int i = ty + 16 * a, j = tx + 16 * b;
       if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc[a][b];
     }
+}
+
+// A 64 x 64 tile product on FP64 FMAs or (OZ, for more than THIN_NC
+// columns) on the tensor cores in FP64 precision; a kernel instantiated with
+// OZ = true is launched with OZ_SMEM bytes of dynamic shared memory.
+template <bool OZ>
+__device__ inline void tile_gemm(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int mr,
+                                 int nc, int K, double alpha) {
+  if (OZ && nc > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<false>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
+  } else {
+    tile_gemm_64(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+  }
 }
 
 // A22 -= L21 U12 ; grid (coltiles, rowtiles, items)
@@ -393,7 +408,7 @@ static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) { ipiv_to_
 
 // trailing update after diagonal block k0: lower -> rows below, upper -> rows
 // above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)
-template <int LOWER>
+template <int LOWER, bool OZ = false>
 static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* items, int k0) {
   SolveItem it = items[blockIdx.z];
   int n = it.n;
@@ -409,8 +424,8 @@ static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* item
   }
   int i0 = r0 + blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (i0 >= r1 || j0 >= it.ncols) return;
-  tile_gemm_64(it.a + i0 + (size_t)k0 * it.ld, it.ld, it.x + k0 + (size_t)j0 * it.ldx, it.ldx,
-               it.x + i0 + (size_t)j0 * it.ldx, it.ldx, r1 - i0, it.ncols - j0, nb, -1.0);
+  tile_gemm<OZ>(it.a + i0 + (size_t)k0 * it.ld, it.ld, it.x + k0 + (size_t)j0 * it.ldx, it.ldx,
+                it.x + i0 + (size_t)j0 * it.ldx, it.ldx, r1 - i0, it.ncols - j0, nb, -1.0);
 }
 
 }  // namespace aifmm

@@ -620,6 +620,7 @@ __global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
 
 // L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R.
 // grid (tiles over r_old, tiles over rn, 2 * cnt); Lm zeroed beforehand
+template <bool OZ>
 __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   int t = blockIdx.z >> 1, side = blockIdx.z & 1;
   if (c.skip[t]) return;
@@ -630,8 +631,14 @@ __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   const double* Q = qbase(c, t, side, M);
   const double* B = side == 0 ? v.u(b) : v.v(b);
   double* Lm = c.Lm + ((size_t)t * 2 + side) * v.R * v.R;
-  tile_gemm_64_tn(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0,
-                  ro - j0, m, 1.0);
+  if (OZ && ro - j0 > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<true>(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R,
+                          min(64, rn - i0), min(64, ro - j0), m, 1.0, oz_dyn);
+  } else {
+    tile_gemm_64_tn(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0,
+                    ro - j0, m, 1.0);
+  }
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, ro - j0) * m);
 }
 
@@ -675,6 +682,7 @@ __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
 // row side fill-ins: M2P_bq -> A_bq += U~^T M2P_bq ; P2P_bq -> P2L_bq = U~^T P2P_bq
 // (the P2L block is zero before b is eliminated).  grid (ns5 * tpc, tiles
 // over rn, cnt) with tpc column tiles per block.
+template <bool OZ>
 __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
   int s = blockIdx.x / tpc, tj = blockIdx.x % tpc, t = blockIdx.z;
   if (c.skip[t]) return;
@@ -693,8 +701,15 @@ __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
   bool elim = colour_of(q, v.d) < c.col;
   double* dst = elim ? v.ly(b, slot6(bc, q, v.d)) : v.lx(b, s);
   const double* Q = c.Q + ((size_t)t * 2) * v.M * v.M;
-  tile_gemm_64_tn(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld, dst + i0 + (size_t)j0 * v.R, v.R,
-                  rn - i0, sw.cols - j0, sw.rows, 1.0);
+  if (OZ && sw.cols - j0 > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<true>(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld,
+                          dst + i0 + (size_t)j0 * v.R, v.R, min(64, rn - i0), min(64, sw.cols - j0), sw.rows, 1.0,
+                          oz_dyn);
+  } else {
+    tile_gemm_64_tn(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld, dst + i0 + (size_t)j0 * v.R,
+                    v.R, rn - i0, sw.cols - j0, sw.rows, 1.0);
+  }
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, sw.cols - j0) * sw.rows);
 }
 
@@ -796,6 +811,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
 // column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
 // (the M2P block into y_b is zero before b is eliminated).
 // grid (ns5 * tpr, tiles over rn, cnt) with tpr row tiles per block.
+template <bool OZ>
 __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
   int s = blockIdx.x / tpr, ti = blockIdx.x % tpr, t = blockIdx.z;
   if (c.skip[t]) return;
@@ -823,8 +839,8 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
     ldd = v.M;
   }
   const double* Q = qbase(c, t, 1, v.M);
-  tile_gemm_64(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd, sw.rows - i0,
-               rn - j0, sw.cols, 1.0);
+  tile_gemm<OZ>(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd,
+                min(64, sw.rows - i0), min(64, rn - j0), sw.cols, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, sw.rows - i0) * (double)min(64, rn - j0) * sw.cols);
 }
 
@@ -1366,7 +1382,12 @@ static int factor_level(Handle& h, int l) {
     AIFMM_CUDA_TRY(h, cudaMemsetAsync(c.Lm, 0, sizeof(double) * (size_t)cnt * 2 * F.R * F.R, st));
     {
       const int rt = (F.R + 63) / 64;
-      k_cmp_lmat<<<dim3(rt, rt, 2 * cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+      if (h.fma_gemm) {
+        k_cmp_lmat<false><<<dim3(rt, rt, 2 * cnt), 256, 0, st>>>(v, c);
+      } else {
+        k_cmp_lmat<true><<<dim3(rt, rt, 2 * cnt), 256, OZ_SMEM, st>>>(v, c);
+      }
+      ++h.nlaunch;
     }
     dp.end();
     dp.begin("row_transform");
@@ -1374,7 +1395,12 @@ static int factor_level(Handle& h, int l) {
     dp.end();
     dp.begin("row_fill");
     const int tpc = (F.M + 63) / 64, rtl = (F.R + 63) / 64;
-    k_cmp_row_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
+    if (h.fma_gemm) {
+      k_cmp_row_fill<false><<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc);
+    } else {
+      k_cmp_row_fill<true><<<dim3(F.ns5 * tpc, rtl, cnt), 256, OZ_SMEM, st>>>(v, c, tpc);
+    }
+    ++h.nlaunch;
     dp.end();
     dp.begin("row_done");
     k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
@@ -1383,7 +1409,12 @@ static int factor_level(Handle& h, int l) {
     k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     dp.begin("col_fill");
-    k_cmp_col_fill<<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc); ++h.nlaunch;
+    if (h.fma_gemm) {
+      k_cmp_col_fill<false><<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc);
+    } else {
+      k_cmp_col_fill<true><<<dim3(F.ns5 * tpc, rtl, cnt), 256, OZ_SMEM, st>>>(v, c, tpc);
+    }
+    ++h.nlaunch;
     dp.end();
     dp.begin("col_done");
     k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
@@ -1436,8 +1467,12 @@ static int factor_level(Handle& h, int l) {
     dp.end();
     {
       // blocked LU solve of Z (interchanges applied by k_z_build): unit-lower
-      // blocks downwards, upper blocks upwards, each diagonal block one warp
-      // per column, each trailing update a tiled GEMM
+      // blocks downwards, upper blocks upwards, each trailing update a tiled
+      // GEMM on FP64 FMAs.  (Not the tensor-core tile: a column of Z mixes
+      // the x part, of size ~1/A_ii, with the z part, orders of magnitude
+      // larger, inside one 64-row chunk, and the digits of the small entries
+      // keep only 49 bits below the chunk's largest -- measured, the lost
+      // accuracy shows up as higher compression ranks at the next level.)
       dp.begin("lus");
       const int ctiles = (e.ncmax + 63) / 64;
       const int wstr = (e.ncmax + 3) / 4, cstr = (e.ncmax + 127) / 128;
@@ -1450,7 +1485,8 @@ static int factor_level(Handle& h, int l) {
         }
         ++h.nlaunch;
         if (k0 + TB < F.P) {
-          k_lus_update<1><<<dim3(ctiles, (F.P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
+          k_lus_update<1, false><<<dim3(ctiles, (F.P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0);
+          ++h.nlaunch;
         }
       }
       for (int k0 = ((F.P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
@@ -1461,7 +1497,8 @@ static int factor_level(Handle& h, int l) {
         }
         ++h.nlaunch;
         if (k0 > 0) {
-          k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0); ++h.nlaunch;
+          k_lus_update<0, false><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0);
+          ++h.nlaunch;
         }
       }
       dp.end();
@@ -1546,6 +1583,10 @@ int run_factor(Handle& h) {
   if (!h.dacc) return HOOM;
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_schur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_lmat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_row_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_col_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+
   {
     // tallest LU panel kept in shared memory: (rows x 32) doubles within the
     // opt-in limit of the device

@@ -80,8 +80,10 @@ __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// C[0..mr, 0..nc] += alpha * A[0..mr, 0..K) B[0..K, 0..nc]; A column-major
-// (lda), B column-major (ldb), C column-major (ldc).  smem: OZ_SMEM bytes.
+// C[0..mr, 0..nc] += alpha * op(A)[0..mr, 0..K) B[0..K, 0..nc]; op(A) = A
+// column-major (lda) or, with TA, A^T for A column-major K x mr (lda);
+// B column-major (ldb), C column-major (ldc).  smem: OZ_SMEM bytes.
+template <bool TA = false>
 __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                        int mr, int nc, int K, double alpha, unsigned char* smem) {
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [OZ_S][64][OZ_LD]
@@ -101,26 +103,46 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
 
   for (int k0 = 0; k0 < K; k0 += OZ_KC) {
     const int kc = min(OZ_KC, K - k0);
-    // ---- stage: exponents (rows of A, columns of B over this chunk)
+    // ---- stage: exponents (rows of op(A), columns of B over this chunk)
     if (tid < 128) (tid < 64 ? ea : eb)[tid & 63] = 0;
     __syncthreads();
-    // A: warp w takes k = 8w..8w+7, lanes the rows lane and lane + 32
+    // A: warp w takes k = 8w..8w+7, lanes the rows lane and lane + 32 (with
+    // TA: warp w the rows 8w..8w+7, lanes k = lane and lane + 32, so that the
+    // loads stay coalesced)
     double av[8][2];
-    int am0 = 0, am1 = 0;
+    if (!TA) {
+      int am0 = 0, am1 = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int k = 8 * w + q;
+      for (int q = 0; q < 8; ++q) {
+        int k = 8 * w + q;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int i = lane + 32 * h;
-        double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
-        av[q][h] = x;
-        int e = oz_bexp(x);
-        if (h == 0) am0 = max(am0, e); else am1 = max(am1, e);
+        for (int h = 0; h < 2; ++h) {
+          int i = lane + 32 * h;
+          double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
+          av[q][h] = x;
+          int e = oz_bexp(x);
+          if (h == 0) am0 = max(am0, e); else am1 = max(am1, e);
+        }
+      }
+      atomicMax(&ea[lane], am0);
+      atomicMax(&ea[lane + 32], am1);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int i = 8 * w + q;
+        int am = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int k = lane + 32 * h;
+          double x = (i < mr && k < kc) ? A[(k0 + k) + (size_t)i * lda] : 0.0;
+          av[q][h] = x;
+          am = max(am, oz_bexp(x));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+        if (lane == 0) ea[i] = am;
       }
     }
-    atomicMax(&ea[lane], am0);
-    atomicMax(&ea[lane + 32], am1);
     // B: warp w takes columns 8w..8w+7, lanes k = lane and lane + 32
     double bv[8][2];
 #pragma unroll
@@ -142,10 +164,10 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
     // ---- stage: digits into shared memory
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      int k = 8 * w + q;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int i = lane + 32 * h;
+        int i = TA ? 8 * w + q : lane + 32 * h;
+        int k = TA ? lane + 32 * h : 8 * w + q;
         oz_digits(av[q][h], ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
       }
     }
