@@ -206,6 +206,10 @@ struct Cmp {
   int* rold;           // [cnt] rank before compression
   int* skip;           // [cnt] 1 if nothing is pending
   double* Lm;          // [cnt][2][R*R] L_b (side 0), R_b (side 1), ld R
+  double* T;           // [cnt][2][R*WC] Q0^T X of the projections, ld R
+  double* tau;         // [cnt][2] RRQR threshold eps * max_j ||F_j|| of the fill-in columns
+  int phase;           // k_cmp_qrcp: 1 = QR of the basis columns, 2 = QRCP of the projected fill-ins
+  int ccap;            // k_cmp_qrcp: column capacity of the phase (shared-memory norms)
   double eps;
   double* flops;       // device accumulator of algorithmic flops (compress group)
   int* err;
@@ -322,9 +326,20 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
   c.skip[t] = (v.m[b] == 0 || (c.nc[2 * t] == rb && (c.sym || c.nc[2 * t + 1] == rb))) ? 1 : 0;
 }
 
-// Householder QR with column pivoting; the first nf = r_b columns are taken
-// in order, then the largest residual column among the fill-ins while its
-// norm exceeds eps * max_j ||F_j||.  Produces Q[:, :rank] explicitly.
+// Column-space compression of [U_b | F] in three steps with the same result,
+// in exact arithmetic, as one Householder QR whose first r_b columns are
+// taken in order and whose later columns are pivoted (reading R3):
+//   phase 1  Householder QR of W[:, :nf] = U_b (nf = r_b, no pivoting): Q0;
+//   k_cmp_ptq / k_cmp_pqt   F := F - Q0 (Q0^T F) as tiled GEMMs (the work
+//            that the forced reflectors did as rank-1 updates of every
+//            fill-in column);
+//   phase 2  Householder QR with column pivoting of the projected F: the
+//            largest residual column while its norm exceeds
+//            tau = eps * max_j ||F_j|| (norms of the fill-ins before the
+//            projection, k_cmp_tau); Q' = Q[:, nf:rank], then made orthogonal
+//            to Q0 once more (the projection leaves Q0 components of size
+//            u ||F_j|| / |R_kk|).
+// Produces Q[:, :rank] explicitly, rank = nf + (phase-2 columns).
 // One thread-block cluster of QC CTAs per (box, side) (QC chosen per level
 // by the host so that the colour's clusters fill the GPU); CTA c owns the
 // columns j with j % QC == c and keeps their residual norms in shared memory.
@@ -350,27 +365,29 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
   extern __shared__ double dyn[];
   __shared__ double shv[32];
   __shared__ int shi[32];
-  __shared__ double shs[32];
   __shared__ ArgMax lbest[2];
-  __shared__ double lmax;
   const int cr = (int)cl.block_rank();
   const int bs = blockIdx.x / QC;
   const int t = c.sym ? bs : bs >> 1, side = c.sym ? 0 : bs & 1;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
-  const int m = v.m[b], n = c.nc[t * 2 + side], nf = c.rold[t];
+  const int nf0 = c.rold[t];
+  // phase 1: the basis columns only, all taken in order; phase 2: the
+  // projected fill-in columns W[:, nf0:], all pivoted, into Q[:, nf0:]
+  const int coff = c.phase == 2 ? nf0 : 0;
+  const int m = v.m[b], nc_all = c.nc[t * 2 + side];
+  const int n = c.phase == 2 ? nc_all - nf0 : nf0, nf = c.phase == 2 ? 0 : nf0;
   const int M = v.M;
-  double* W = c.W + ((size_t)t * 2 + side) * M * c.WC;
-  double* Q = c.Q + ((size_t)t * 2 + side) * M * M;
-  const int cw = (c.WC + QC - 1) / QC;
+  double* W = c.W + ((size_t)t * 2 + side) * M * c.WC + (size_t)coff * M;
+  double* Q = c.Q + ((size_t)t * 2 + side) * M * M + (size_t)coff * M;
+  const int cw = (c.ccap + QC - 1) / QC;
   double* vbuf = dyn;                                    // [2][M]
   int* pivs = reinterpret_cast<int*>(dyn + 2 * M);       // [M]
   double* cnl = dyn + 2 * M + (M + 1) / 2;               // [cw] squared residual norms (-1: retired)
   double* cref = cnl + cw;                               // [cw] value at the last exact computation
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nloc = n > cr ? (n - cr + QC - 1) / QC : 0;   // own columns j = cr + QC * jl
-  // initial residual norms of the own fill-in columns, and the threshold
-  double mx = 0.0;
+  // initial residual norms of the own pivoted columns
   for (int jl = w; jl < nloc; jl += nw) {
     int j = cr + QC * jl;
     double acc = 0.0;
@@ -378,21 +395,10 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
       for (int i = lane; i < m; i += 32) acc += W[i + (size_t)j * M] * W[i + (size_t)j * M];
     acc = warp_sum(acc);
     if (lane == 0) cnl[jl] = cref[jl] = acc;
-    mx = fmax(mx, acc);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) shs[w] = mx;
+  const double tau = c.tau[t * 2 + side];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int q = 0; q < nw; ++q) a = fmax(a, shs[q]);
-    lmax = a;
-  }
-  cl.sync();
-  double gmax = 0.0;
-  for (int r = 0; r < QC; ++r) gmax = fmax(gmax, *cl.map_shared_rank(&lmax, r));
-  const double tau = c.eps * sqrt(gmax);
-  const int kmax = min(m, n);
+  const int kmax = min(m - coff, n);     // the projected columns lie in m - nf0 dimensions
   int k = 0;
   for (; k < kmax; ++k) {
     double* vref = vbuf + (size_t)(k & 1) * M;
@@ -550,12 +556,99 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
     }
   }
   if (cr == 0 && threadIdx.x == 0) {
-    c.rk[t * 2 + side] = rank;
-    if (c.sym) c.rk[t * 2 + 1] = rank;
+    if (c.phase == 2) {
+      c.rk[t * 2 + side] = nf0 + rank;
+      if (c.sym) c.rk[t * 2 + 1] = nf0 + rank;
+    }
     double f = 2.0 * m * (n - nf);
     for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
     atomicAdd(c.flops, f);
   }
+}
+
+// RRQR threshold of each box side: tau = eps * max_j ||F_j|| over the
+// gathered fill-in columns W[:, nf0:nc] (before any projection); grid
+// (cnt * sides), 256 threads
+__global__ void __launch_bounds__(256) k_cmp_tau(LV v, Cmp c) {
+  __shared__ double shm[8];
+  const int nsd = c.sym ? 1 : 2;
+  const int t = blockIdx.x / nsd, side = blockIdx.x % nsd;
+  if (c.skip[t]) return;
+  const int b = cbox(c, v, t);
+  const int m = v.m[b], M = v.M, nf0 = c.rold[t], n = c.nc[t * 2 + side];
+  const double* W = c.W + ((size_t)t * 2 + side) * M * c.WC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double mx = 0.0;
+  for (int j = nf0 + w; j < n; j += 8) {
+    double a = 0.0;
+    for (int i = lane; i < m; i += 32) a += W[i + (size_t)j * M] * W[i + (size_t)j * M];
+    mx = fmax(mx, warp_sum(a));
+  }
+  if (lane == 0) shm[w] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < 8; ++q) a = fmax(a, shm[q]);
+    c.tau[t * 2 + side] = c.eps * sqrt(a);
+    atomicAdd(c.flops, 2.0 * m * (double)(n - nf0));
+  }
+}
+
+// X := X - Q0 (Q0^T X) with Q0 = Q[:, :nf0] (the orthonormalised basis) and
+// X = W[:, nf0:nc] (what 0: the fill-in columns) or X = Q[:, nf0:rank]
+// (what 1: the new basis columns, once more).  Two launches: k_cmp_ptq
+// T = Q0^T X (each CTA first clears its tile of T), k_cmp_pqt X -= Q0 T.
+__device__ inline int proj_cols(const Cmp& c, int t, int side, int nf0, int what) {
+  return (what == 0 ? c.nc[t * 2 + side] : c.rk[t * 2 + side]) - nf0;
+}
+
+// grid (tiles over X's columns, tiles over nf0, cnt * sides)
+template <bool OZ>
+__global__ void __launch_bounds__(256) k_cmp_ptq(LV v, Cmp c, int what) {
+  const int nsd = c.sym ? 1 : 2;
+  const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
+  if (c.skip[t]) return;
+  const int b = cbox(c, v, t);
+  const int m = v.m[b], M = v.M, nf0 = c.rold[t];
+  const int ncx = proj_cols(c, t, side, nf0, what);
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= nf0 || j0 >= ncx) return;
+  const double* Q0 = c.Q + ((size_t)t * 2 + side) * M * M;
+  const double* X = (what == 0 ? c.W + ((size_t)t * 2 + side) * M * c.WC : Q0) + (size_t)nf0 * M;
+  double* T = c.T + ((size_t)t * 2 + side) * (size_t)v.R * c.WC + i0 + (size_t)j0 * v.R;
+  const int mr = min(64, nf0 - i0), nc = min(64, ncx - j0);
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    int i = e & 63, j = e >> 6;
+    if (i < mr && j < nc) T[i + (size_t)j * v.R] = 0.0;
+  }
+  __syncthreads();
+  if (OZ && nc > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<true>(Q0 + (size_t)i0 * M, M, X + (size_t)j0 * M, M, T, v.R, mr, nc, m, 1.0, oz_dyn);
+  } else {
+    tile_gemm_64_tn(Q0 + (size_t)i0 * M, M, X + (size_t)j0 * M, M, T, v.R, mr, nc, m, 1.0);
+  }
+  if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * mr * (double)nc * m);
+}
+
+// grid (tiles over X's columns, tiles over m, cnt * sides)
+template <bool OZ>
+__global__ void __launch_bounds__(256) k_cmp_pqt(LV v, Cmp c, int what) {
+  const int nsd = c.sym ? 1 : 2;
+  const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
+  if (c.skip[t]) return;
+  const int b = cbox(c, v, t);
+  const int m = v.m[b], M = v.M, nf0 = c.rold[t];
+  const int ncx = proj_cols(c, t, side, nf0, what);
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (nf0 == 0 || i0 >= m || j0 >= ncx) return;
+  const double* Q0 = c.Q + ((size_t)t * 2 + side) * M * M;
+  double* X = (what == 0 ? c.W + ((size_t)t * 2 + side) * M * c.WC : c.Q + ((size_t)t * 2 + side) * M * M) +
+              (size_t)nf0 * M;
+  const double* T = c.T + ((size_t)t * 2 + side) * (size_t)v.R * c.WC + (size_t)j0 * v.R;
+  const int mr = min(64, m - i0), nc = min(64, ncx - j0);
+  tile_gemm<OZ>(Q0 + i0, M, T, v.R, X + i0 + (size_t)j0 * M, M, mr, nc, nf0, -1.0);
+  if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * mr * (double)nc * nf0);
 }
 
 // equal ranks: the smaller side takes the other side's extra basis columns
@@ -1332,7 +1425,9 @@ static int factor_level(Handle& h, int l) {
     c.cn = (double*)hscratch(h, 22, sizeof(double) * (size_t)cnt * 2 * c.WC);
     int* ib = (int*)hscratch(h, 23, sizeof(int) * (size_t)cnt * 8);
     c.Lm = (double*)hscratch(h, 24, sizeof(double) * (size_t)cnt * 2 * F.R * F.R);
-    if (!c.W || !c.Q || !c.cn || !ib || !c.Lm) return HOOM;
+    c.T = (double*)hscratch(h, 32, sizeof(double) * (size_t)cnt * 2 * F.R * c.WC);
+    c.tau = (double*)hscratch(h, 33, sizeof(double) * (size_t)cnt * 2);
+    if (!c.W || !c.Q || !c.cn || !ib || !c.Lm || !c.T || !c.tau) return HOOM;
     c.nc = ib;
     c.rk = ib + 2 * cnt;
     c.rn = ib + 4 * cnt;
@@ -1343,38 +1438,66 @@ static int factor_level(Handle& h, int l) {
     k_cmp_gather<<<dim3(cnt, nsides), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
-    dp.begin("qrcp");
     {
-      // one cluster of qc CTAs per box side (skipped boxes exit at once);
-      // qc so that the colour's clusters give about two CTAs per SM
+      // threshold from the fill-in columns as gathered
+      dp.begin("tau");
+      k_cmp_tau<<<cnt * nsides, 256, 0, st>>>(v, c); ++h.nlaunch;
+      dp.end();
+      // phase 1 (QR of U_b) in clusters of two CTAs; phase 2 (QRCP of the
+      // projected fill-ins) in clusters of qc CTAs, qc so that the colour's
+      // clusters give about two CTAs per SM
       int qc = 2;
       while (qc < 16 && qc * nsides * cnt < 2 * h.nsm) qc *= 2;
-      cudaLaunchConfig_t cfg = {};
-      // few clusters (top levels): wider CTAs, fewer columns per warp
-      const int ncta = qc * nsides * cnt;
-      cfg.gridDim = dim3(ncta);
-      cfg.blockDim = dim3(ncta <= h.nsm ? 1024 : ncta <= 2 * h.nsm ? 512 : 256);
-      cfg.dynamicSmemBytes = sizeof(double) * (2 * (size_t)F.M + (F.M + 1) / 2 + 2 * (size_t)((c.WC + qc - 1) / qc));
-      if (cfg.dynamicSmemBytes > (size_t)h.smem_optin) {
-        h.err = "compress: a box side needs " + std::to_string(cfg.dynamicSmemBytes) +
-                " bytes of shared memory per CTA";
-        return HCAPACITY;
+      int maxr = 1;
+      for (int b = 0; b < F.nb; ++b) maxr = std::max(maxr, F.h_r[b]);
+      const int ptiles_r = (maxr + 63) / 64;
+      for (int phase = 1; phase <= 2; ++phase) {
+        const int q = phase == 1 ? 2 : qc;
+        c.phase = phase;
+        c.ccap = phase == 1 ? F.R : c.WC;
+        cudaLaunchConfig_t cfg = {};
+        const int ncta = q * nsides * cnt;
+        cfg.gridDim = dim3(ncta);
+        // few clusters (top levels): wider CTAs, fewer columns per warp
+        cfg.blockDim = dim3(ncta <= h.nsm ? 1024 : ncta <= 2 * h.nsm ? 512 : 256);
+        cfg.dynamicSmemBytes =
+            sizeof(double) * (2 * (size_t)F.M + (F.M + 1) / 2 + 2 * (size_t)((c.ccap + q - 1) / q));
+        if (cfg.dynamicSmemBytes > (size_t)h.smem_optin) {
+          h.err = "compress: a box side needs " + std::to_string(cfg.dynamicSmemBytes) +
+                  " bytes of shared memory per CTA";
+          return HCAPACITY;
+        }
+        if (cfg.dynamicSmemBytes > 48 * 1024)
+          AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)cfg.dynamicSmemBytes));
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = q;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        dp.begin(phase == 1 ? "qr_basis" : "qrcp_fill");
+        AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, c));
+        ++h.nlaunch;
+        dp.end();
+        // phase 1 -> project the fill-ins; phase 2 -> the new basis columns
+        const int what = phase == 1 ? 0 : 1;
+        const int ncx = what == 0 ? c.WC : F.M;
+        const dim3 g1((ncx + 63) / 64, ptiles_r, cnt * nsides), g2((ncx + 63) / 64, (F.M + 63) / 64, cnt * nsides);
+        dp.begin(phase == 1 ? "project_fill" : "project_basis");
+        if (h.fma_gemm) {
+          k_cmp_ptq<false><<<g1, 256, 0, st>>>(v, c, what);
+          k_cmp_pqt<false><<<g2, 256, 0, st>>>(v, c, what);
+        } else {
+          k_cmp_ptq<true><<<g1, 256, OZ_SMEM, st>>>(v, c, what);
+          k_cmp_pqt<true><<<g2, 256, OZ_SMEM, st>>>(v, c, what);
+        }
+        h.nlaunch += 2;
+        dp.end();
       }
-      if (cfg.dynamicSmemBytes > 48 * 1024)
-        AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)cfg.dynamicSmemBytes));
-      cfg.stream = st;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = qc;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, c));
-      ++h.nlaunch;
     }
-    dp.end();
     dp.begin("equalise");
     k_cmp_equalise<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
@@ -1472,7 +1595,10 @@ static int factor_level(Handle& h, int l) {
       // the x part, of size ~1/A_ii, with the z part, orders of magnitude
       // larger, inside one 64-row chunk, and the digits of the small entries
       // keep only 49 bits below the chunk's largest -- measured, the lost
-      // accuracy shows up as higher compression ranks at the next level.)
+      // accuracy shows up as higher compression ranks at the next level.
+      // Rescaling each row of the chunk by its own power of two before the
+      // digits are cut halved the Z-solve time but still raised the ranks:
+      // 16% more factorisation flops and no net gain at 65,536 points.)
       dp.begin("lus");
       const int ctiles = (e.ncmax + 63) / 64;
       const int wstr = (e.ncmax + 3) / 4, cstr = (e.ncmax + 127) / 128;
@@ -1586,6 +1712,8 @@ int run_factor(Handle& h) {
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_lmat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_row_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_col_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_ptq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_pqt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
 
   {
     // tallest LU panel kept in shared memory: (rows x 32) doubles within the

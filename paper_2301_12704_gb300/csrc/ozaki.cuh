@@ -239,7 +239,7 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
             float wgt = 1.0f;
 #pragma unroll
             for (int x = 0; x < 5; ++x) {
-              tot += (long long)__float2int_rn(acc[x][a][b][q] * wgt) << (7 * (4 - x));
+              tot += (long long)__float2int_rn(acc[x][a][b][q] * wgt) * (1ll << (7 * (4 - x)));
               wgt *= 128.0f;
             }
             double sum = fma((double)tot, 0x1p-28, (double)acc[5][a][b][q]);
