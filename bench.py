@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--mixed3d", type=int, default=0,
+                   help="also run the 3D mixed-precision GMRES configuration at this many points")
     return p.parse_args()
 
 
@@ -184,15 +186,16 @@ def serve(A, w, pts, stream, dev, requests=64, seed=4):
             "note": "sequential solve requests against one resident factorisation; host rhs in, host x out"}
 
 
-def gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-6, rtol=1e-10):
+def gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-6, rtol=1e-10, fp32=False):
     """AIFMM as a preconditioner (Sec. 4, Experiment 5): a factorisation with
-    a looser compress threshold, then FP64 GMRES on the H^2 product."""
+    a looser compress threshold (and, with fp32, FP32 tile products), then
+    FP64 GMRES on the H^2 product."""
     import torch
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    h = A.aifmm_build(pts_d, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream, factor_tol=ftol)
+    h = A.aifmm_build(pts_d, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream, factor_tol=ftol, fp32=fp32)
     A.aifmm_factor(h)                                   # warm
     A.aifmm_destroy(h)
-    h = A.aifmm_build(pts_d, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream, factor_tol=ftol)
+    h = A.aifmm_build(pts_d, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream, factor_tol=ftol, fp32=fp32)
     ev[0].record(stream)
     A.aifmm_factor(h)
     ev[1].record(stream)
@@ -204,9 +207,50 @@ def gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-6, rtol=1e-10):
     true = float(torch.linalg.norm(r) / torch.linalg.norm(b1_d[:, 0]))
     A.aifmm_destroy(h)
     tf, tg = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    return {"factor_tol": ftol, "rtol": rtol, "ms_factor": tf, "ms_gmres": tg, "iterations": it,
+    return {"factor_tol": ftol, "products": "fp32" if fp32 else "fp64", "rtol": rtol, "ms_factor": tf,
+            "ms_gmres": tg, "iterations": it,
             "relres_h2": rr, "residual_direct_sum": true, "max_rank": st["max_rank_factor"],
             "points_per_s": w.n / ((tf + tg) / 1e3)}
+
+
+def mixed3d(A, dev, n=32768, rtol=1e-10):
+    """The 3D mixed-precision configuration (1/r, A_ii = N^(2/3), uniform in
+    [-1,1]^3, seed 2, leaf 64, tol 1e-6): the factorisation with FP32 tile
+    products as the preconditioner of FP64 GMRES on the H^2 product, beside
+    the same with FP64 products; points/s = N / (T_factor + T_gmres).  N is
+    the largest size whose capacity-padded blocks fit one GB300 (262,144
+    points would need several hundred GB)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    w = W.invr3d(n, seed=2)
+    pts, b = W.points_and_rhs(w)
+    pts_d = torch.from_numpy(pts).to(dev)
+    b_d = torch.from_numpy(np.asfortranarray(b)).to(dev)[:, 0]
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": f"invr3d N={n}: uniform [-1,1]^3 (seed 2), A_ij=1/|x_i-x_j|, A_ii=N^(2/3), leaf 64, "
+                       f"NNCA and compress tol 1e-6, GMRES rtol {rtol:g}"}
+    for fp32 in (True, False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            h = A.aifmm_build(pts_d, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream, fp32=fp32)
+            ev[1].record(stream)
+            A.aifmm_factor(h)
+            ev[2].record(stream)
+            x, it, rr = A.aifmm_gmres(h, b_d, rtol=rtol, maxit=200, restart=40, use_precond=True)
+            ev[3].record(stream)
+        stream.synchronize()
+        st = A.aifmm_stats(h)
+        r = A.aifmm_direct_matvec(h, x)[:, 0] - b_d
+        true = float(torch.linalg.norm(r) / torch.linalg.norm(b_d))
+        A.aifmm_destroy(h)
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(3)]
+        out["fp32" if fp32 else "fp64"] = {
+            "ms_build": t[0], "ms_factor": t[1], "ms_gmres": t[2], "iterations": it, "relres_h2": rr,
+            "residual_direct_sum": true, "levels": st["levels"], "max_rank": st["max_rank_factor"],
+            "gb_resident": st["bytes_resident"] / 1e9, "points_per_s": n / ((t[1] + t[2]) / 1e3)}
+    return out
 
 
 def main():
@@ -345,7 +389,10 @@ def main():
                               "the host points enter through aifmm_build, which the metric excludes"}
     if not args.no_serve:
         out["serve"] = serve(A, w, pts, stream, dev)
-        out["gmres_mode"] = gmres_mode(A, w, pts_d, b1_d, stream)
+        out["gmres_mode"] = gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-4)
+        out["gmres_mode_fp32"] = gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-4, fp32=True)
+    if args.mixed3d:
+        out["mixed3d"] = mixed3d(A, dev, n=args.mixed3d)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:

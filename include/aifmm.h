@@ -87,6 +87,18 @@ typedef struct {
   int fma_gemm;    /* 0 (default): the Schur-update tile products run on the BF16
                       tensor cores in FP64 precision (exact 7-bit integer digits,
                       see aifmm_kernels.h); 1: on FP64 FMAs */
+  int tcgen05;     /* 1: the Schur-update tiles issue the same digit products on the
+                      5th-generation tensor cores (tcgen05.mma, accumulators in tensor
+                      memory; aifmm_dgemm_tc05) instead of warp MMAs; same accuracy,
+                      slower on the short tiles of these factorisations.  0 (default) */
+  int precision;   /* 0 (default): FP64 arithmetic throughout.  1: the tile products of
+                      the factorisation (Schur update, Z = Piv^-1 B, the pivot LU's
+                      trailing updates, the compress fills and projections) in FP32
+                      with FP32 sums, operands and results kept in FP64; the pivoted
+                      QR that fixes the compression ranks, the panels and the
+                      triangular blocks stay FP64.  A factorisation for preconditioning
+                      aifmm_gmres (Sec. 4, AIFMM as a preconditioner); aifmm_solve with
+                      it has a relative error of about 1e-6 */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of

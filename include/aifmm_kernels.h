@@ -26,6 +26,17 @@ extern "C" {
 int aifmm_dgemm_tc(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                    int k, double alpha, void* stream);
 
+/* The same product on the 5th-generation tensor cores: tcgen05.mma with
+ * BF16 digit operands in shared memory and FP32 accumulators in tensor
+ * memory (two digits of A stacked per 128-row MMA), the exact digit-pair
+ * sums combined in 64-bit integer fixed point across K and converted to
+ * FP64 once per output.  Same digits and rounding rules as aifmm_dgemm_tc;
+ * k <= 8192.  Arguments as aifmm_dgemm_tc; additionally returns 7
+ * (AIFMM_ERR_TIMEOUT) if a bounded wait for the tensor cores ran out (C is
+ * then left unchanged for the tiles concerned). */
+int aifmm_dgemm_tc05(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
+                     int k, double alpha, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ class Kernel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("no_symmetry", C.c_int), ("factor_tol", C.c_double), ("fma_gemm", C.c_int)]
+                ("no_symmetry", C.c_int), ("factor_tol", C.c_double), ("fma_gemm", C.c_int),
+                ("tcgen05", C.c_int), ("precision", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -74,6 +75,8 @@ def lib():
         L.aifmm_stats.argtypes = [vp, C.POINTER(Stats)]
         L.aifmm_dgemm_tc.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
         L.aifmm_dgemm_tc.restype = C.c_int
+        L.aifmm_dgemm_tc05.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
+        L.aifmm_dgemm_tc05.restype = C.c_int
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
         L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
         L.aifmm_level_pivots.argtypes = [vp, cint, vp]
@@ -119,19 +122,23 @@ class Handle:
 
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
                 depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True,
-                factor_tol: float = 0.0, fma_gemm: bool = False) -> Handle:
+                factor_tol: float = 0.0, fma_gemm: bool = False, tcgen05: bool = False,
+                fp32: bool = False) -> Handle:
     """Build tree, lists, NNCA operators and the extended system (C: aifmm_build).
 
     ``symmetric=False`` selects the general elimination (rows and columns
     compressed separately, every Schur block computed); ``factor_tol`` > 0 is
     the compress threshold of the factorisation (default: ``tol``);
-    ``fma_gemm`` runs the Schur tiles on FP64 FMAs instead of the tensor cores."""
+    ``fma_gemm`` runs the Schur tiles on FP64 FMAs instead of the tensor cores;
+    ``tcgen05`` issues them on tcgen05.mma instead of warp MMAs; ``fp32``
+    makes the factorisation's tile products FP32 (a preconditioner for
+    aifmm_gmres)."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
     o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
-                float(factor_tol), int(bool(fma_gemm)))
+                float(factor_tol), int(bool(fma_gemm)), int(bool(tcgen05)), int(bool(fp32)))
     out = C.c_void_p()
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
@@ -225,8 +232,9 @@ def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: in
     return x, it.value, rr.value
 
 
-def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None) -> None:
-    """C_ += alpha A B on the tensor cores in FP64 precision (C: aifmm_dgemm_tc).
+def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = False) -> None:
+    """C_ += alpha A B on the tensor cores in FP64 precision (C: aifmm_dgemm_tc,
+    or aifmm_dgemm_tc05 with ``tcgen05``).
     A, B, C_ CUDA float64 tensors, column-major (e.g. ``t.t().contiguous().t()``)."""
     m, k = A.shape
     k2, n = B.shape
@@ -235,7 +243,8 @@ def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None) -> None:
         assert t.is_cuda and (t.stride(0) == 1 or t.shape[0] == 1), "column-major CUDA tensors"
         return max(1, t.shape[0], t.stride(1) if t.shape[1] > 1 else 1)
 
-    st = lib().aifmm_dgemm_tc(C.c_void_p(A.data_ptr()), ld(A), C.c_void_p(B.data_ptr()), ld(B),
+    fn = lib().aifmm_dgemm_tc05 if tcgen05 else lib().aifmm_dgemm_tc
+    st = fn(C.c_void_p(A.data_ptr()), ld(A), C.c_void_p(B.data_ptr()), ld(B),
                               C.c_void_p(C_.data_ptr()), ld(C_), m, n, k, float(alpha),
                               C.c_void_p(stream) if stream else None)
     if st != 0:

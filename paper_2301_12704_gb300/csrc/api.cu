@@ -144,7 +144,8 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
       !(tol >= 0.0) || leaf_size < 1 || k->kind < 0 || k->kind > 3 || !std::isfinite(k->diag) ||
       (k->kind == AIFMM_K_GAUSS && !(k->length > 0.0)) || (opt && opt->order != 0) ||
       (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12)) ||
-      (opt && !(opt->factor_tol >= 0.0 && std::isfinite(opt->factor_tol)))) {
+      (opt && !(opt->factor_tol >= 0.0 && std::isfinite(opt->factor_tol))) ||
+      (opt && (opt->precision < 0 || opt->precision > 1))) {
     g_build_err = "invalid argument";
     return AIFMM_ERR_INVALID;
   }
@@ -163,6 +164,8 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.profile = opt && opt->profile;
   h.sym = !(opt && opt->no_symmetry);
   h.fma_gemm = opt && opt->fma_gemm;
+  h.tc05 = opt && opt->tcgen05;
+  h.fp32 = opt && opt->precision == 1;
   if (opt && opt->stream) {
     h.stream = (cudaStream_t)opt->stream;
   } else {

@@ -96,28 +96,32 @@ static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int
 // narrow right operand (nc <= 8 columns, e.g. a single right-hand side):
 // 64 rows x 4 slices of K, one thread per (row, slice), every column of B
 // in registers; the slices are summed through shared memory
+// CT: the arithmetic type of the products and sums (double, or float for
+// the FP32 factorisation used as a preconditioner); operands and results
+// stay FP64 in memory.
 constexpr int THIN_NC = 8;
+template <typename CT = double>
 __device__ inline void tile_gemm_64_thin(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                          int mr, int nc, int K, double alpha) {
-  __shared__ double red[4][THIN_NC][64 + 1];
+  __shared__ CT red[4][THIN_NC][64 + 1];
   const int i = threadIdx.x & 63, sl = threadIdx.x >> 6;   // 256 threads
-  double acc[THIN_NC];
+  CT acc[THIN_NC];
 #pragma unroll
-  for (int c = 0; c < THIN_NC; ++c) acc[c] = 0.0;
+  for (int c = 0; c < THIN_NC; ++c) acc[c] = CT(0);
   const int kq = (K + 3) / 4, ka = sl * kq, kb = min(K, ka + kq);
   if (i < mr)
     for (int k = ka; k < kb; ++k) {
-      double a = A[i + (size_t)k * lda];
+      CT a = (CT)A[i + (size_t)k * lda];
 #pragma unroll
       for (int c = 0; c < THIN_NC; ++c)
-        if (c < nc) acc[c] = fma(a, B[k + (size_t)c * ldb], acc[c]);
+        if (c < nc) acc[c] = fma(a, (CT)B[k + (size_t)c * ldb], acc[c]);
     }
 #pragma unroll
   for (int c = 0; c < THIN_NC; ++c) red[sl][c][i] = acc[c];
   __syncthreads();
   for (int e = threadIdx.x; e < 64 * nc; e += blockDim.x) {
     int r = e & 63, c = e >> 6;
-    if (r < mr) C[r + (size_t)c * ldc] += alpha * (((red[0][c][r] + red[1][c][r]) + red[2][c][r]) + red[3][c][r]);
+    if (r < mr) C[r + (size_t)c * ldc] += alpha * (double)(((red[0][c][r] + red[1][c][r]) + red[2][c][r]) + red[3][c][r]);
   }
   __syncthreads();
 }
@@ -126,31 +130,32 @@ __device__ inline void tile_gemm_64_thin(const double* A, int lda, const double*
 // (A column-major lda, B column-major ldb, C column-major ldc), bounds
 // rows < mr, cols < nc.  256 threads, 4x4 outputs each (the thin form above
 // when nc <= THIN_NC).
+template <typename CT = double>
 __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                     int mr, int nc, int K, double alpha) {
   if (nc <= THIN_NC) {
-    tile_gemm_64_thin(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+    tile_gemm_64_thin<CT>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
     return;
   }
-  __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64 + 1];
+  __shared__ CT As[16][64 + 1];
+  __shared__ CT Bs[16][64 + 1];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = CT(0);
   for (int k0 = 0; k0 < K; k0 += 16) {
     for (int e = threadIdx.x; e < 16 * 64; e += 256) {
       int kk = e >> 6, ii = e & 63;
-      As[kk][ii] = (ii < mr && k0 + kk < K) ? A[ii + (size_t)(k0 + kk) * lda] : 0.0;
+      As[kk][ii] = (ii < mr && k0 + kk < K) ? (CT)A[ii + (size_t)(k0 + kk) * lda] : CT(0);
       int jj = e >> 4, k2 = e & 15;
-      Bs[k2][jj] = (jj < nc && k0 + k2 < K) ? B[(k0 + k2) + (size_t)jj * ldb] : 0.0;
+      Bs[k2][jj] = (jj < nc && k0 + k2 < K) ? (CT)B[(k0 + k2) + (size_t)jj * ldb] : CT(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      CT av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
 #pragma unroll
@@ -167,25 +172,34 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc[a][b];
+      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * (double)acc[a][b];
     }
 }
 
-// A 64 x 64 tile product on FP64 FMAs or (OZ, for more than THIN_NC
-// columns) on the tensor cores in FP64 precision; a kernel instantiated with
-// OZ = true is launched with OZ_SMEM bytes of dynamic shared memory.
-template <bool OZ>
+// Product modes of the tile kernels: PM_FMA FP64 FMAs; PM_OZ FP64 precision
+// on the BF16 warp MMAs (ozaki.cuh, for more than THIN_NC columns; kernels
+// instantiated with it are launched with OZ_SMEM bytes of dynamic shared
+// memory); PM_TC05 the same digits on tcgen05 (tc05.cuh, the Schur update
+// only, TC_SMEM bytes); PM_F32 FP32 products and sums of FP64 operands (the
+// factorisation used as a preconditioner).
+enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3 };
+
+// C += alpha A B, 64 x 64 tile (A column-major lda, B column-major ldb)
+template <int PM>
 __device__ inline void tile_gemm(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int mr,
                                  int nc, int K, double alpha) {
-  if (OZ && nc > THIN_NC) {
+  if (PM == PM_OZ && nc > THIN_NC) {
     extern __shared__ unsigned char oz_dyn[];
     tile_gemm_64_oz<false>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
+  } else if (PM == PM_F32) {
+    tile_gemm_64<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
   } else {
     tile_gemm_64(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
   }
 }
 
-// A22 -= L21 U12 ; grid (coltiles, rowtiles, items)
+// A22 -= L21 U12 ; grid (coltiles, rowtiles, items); PM_FMA or PM_F32
+template <int PM = PM_FMA>
 static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int k0) {
   LuItem it = items[blockIdx.z];
   int n = it.n;
@@ -194,8 +208,8 @@ static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int
   if (k0 >= n || i0 >= n || j0 >= n) return;
   double* A = it.a;
   const int ld = it.ld;
-  tile_gemm_64(A + i0 + (size_t)k0 * ld, ld, A + k0 + (size_t)j0 * ld, ld, A + i0 + (size_t)j0 * ld, ld,
-               n - i0, n - j0, kend - k0, -1.0);
+  tile_gemm<PM>(A + i0 + (size_t)k0 * ld, ld, A + k0 + (size_t)j0 * ld, ld, A + i0 + (size_t)j0 * ld, ld,
+                n - i0, n - j0, kend - k0, -1.0);
 }
 
 // X := A^-1 X for an LU-factored A (ipiv interchanges, unit L, U) on a strip
@@ -408,7 +422,7 @@ static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) { ipiv_to_
 
 // trailing update after diagonal block k0: lower -> rows below, upper -> rows
 // above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)
-template <int LOWER, bool OZ = false>
+template <int LOWER, int PM = PM_FMA>
 static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* items, int k0) {
   SolveItem it = items[blockIdx.z];
   int n = it.n;
@@ -424,7 +438,7 @@ static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* item
   }
   int i0 = r0 + blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (i0 >= r1 || j0 >= it.ncols) return;
-  tile_gemm<OZ>(it.a + i0 + (size_t)k0 * it.ld, it.ld, it.x + k0 + (size_t)j0 * it.ldx, it.ldx,
+  tile_gemm<PM>(it.a + i0 + (size_t)k0 * it.ld, it.ld, it.x + k0 + (size_t)j0 * it.ldx, it.ldx,
                 it.x + i0 + (size_t)j0 * it.ldx, it.ldx, r1 - i0, it.ncols - j0, nb, -1.0);
 }
 
@@ -434,26 +448,27 @@ namespace aifmm {
 
 // 64x64 FP64 tile with a transposed left operand:
 // C[0..mr, 0..nc] += alpha * A^T B, A column-major K x mr (lda), B K x nc (ldb)
+template <typename CT = double>
 __device__ inline void tile_gemm_64_tn(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                        int mr, int nc, int K, double alpha) {
-  __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64 + 1];
+  __shared__ CT As[16][64 + 1];
+  __shared__ CT Bs[16][64 + 1];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = CT(0);
   for (int k0 = 0; k0 < K; k0 += 16) {
     for (int e = threadIdx.x; e < 16 * 64; e += 256) {
       int k2 = e & 15, ii = e >> 4;
-      As[k2][ii] = (ii < mr && k0 + k2 < K) ? A[(k0 + k2) + (size_t)ii * lda] : 0.0;
-      Bs[k2][ii] = (ii < nc && k0 + k2 < K) ? B[(k0 + k2) + (size_t)ii * ldb] : 0.0;
+      As[k2][ii] = (ii < mr && k0 + k2 < K) ? (CT)A[(k0 + k2) + (size_t)ii * lda] : CT(0);
+      Bs[k2][ii] = (ii < nc && k0 + k2 < K) ? (CT)B[(k0 + k2) + (size_t)ii * ldb] : CT(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      CT av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
 #pragma unroll
@@ -470,9 +485,24 @@ __device__ inline void tile_gemm_64_tn(const double* A, int lda, const double* B
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc[a][b];
+      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * (double)acc[a][b];
     }
 }
+
+// C += alpha A^T B, 64 x 64 tile (A column-major K x mr, lda)
+template <int PM>
+__device__ inline void tile_gemm_tn(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int mr,
+                                    int nc, int K, double alpha) {
+  if (PM == PM_OZ && nc > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<true>(A, lda, B, ldb, C, ldc, min(64, mr), min(64, nc), K, alpha, oz_dyn);
+  } else if (PM == PM_F32) {
+    tile_gemm_64_tn<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+  } else {
+    tile_gemm_64_tn(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+  }
+}
+
 
 }  // namespace aifmm
 

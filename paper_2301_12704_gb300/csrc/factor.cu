@@ -30,6 +30,7 @@
 #include "internal.h"
 #include "level.cuh"
 #include "ozaki.cuh"
+#include "tc05.cuh"
 
 namespace aifmm {
 
@@ -603,7 +604,7 @@ __device__ inline int proj_cols(const Cmp& c, int t, int side, int nf0, int what
 }
 
 // grid (tiles over X's columns, tiles over nf0, cnt * sides)
-template <bool OZ>
+template <int PM>
 __global__ void __launch_bounds__(256) k_cmp_ptq(LV v, Cmp c, int what) {
   const int nsd = c.sym ? 1 : 2;
   const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
@@ -622,17 +623,12 @@ __global__ void __launch_bounds__(256) k_cmp_ptq(LV v, Cmp c, int what) {
     if (i < mr && j < nc) T[i + (size_t)j * v.R] = 0.0;
   }
   __syncthreads();
-  if (OZ && nc > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
-    tile_gemm_64_oz<true>(Q0 + (size_t)i0 * M, M, X + (size_t)j0 * M, M, T, v.R, mr, nc, m, 1.0, oz_dyn);
-  } else {
-    tile_gemm_64_tn(Q0 + (size_t)i0 * M, M, X + (size_t)j0 * M, M, T, v.R, mr, nc, m, 1.0);
-  }
+  tile_gemm_tn<PM>(Q0 + (size_t)i0 * M, M, X + (size_t)j0 * M, M, T, v.R, mr, nc, m, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * mr * (double)nc * m);
 }
 
 // grid (tiles over X's columns, tiles over m, cnt * sides)
-template <bool OZ>
+template <int PM>
 __global__ void __launch_bounds__(256) k_cmp_pqt(LV v, Cmp c, int what) {
   const int nsd = c.sym ? 1 : 2;
   const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
@@ -647,7 +643,7 @@ __global__ void __launch_bounds__(256) k_cmp_pqt(LV v, Cmp c, int what) {
               (size_t)nf0 * M;
   const double* T = c.T + ((size_t)t * 2 + side) * (size_t)v.R * c.WC + (size_t)j0 * v.R;
   const int mr = min(64, m - i0), nc = min(64, ncx - j0);
-  tile_gemm<OZ>(Q0 + i0, M, T, v.R, X + i0 + (size_t)j0 * M, M, mr, nc, nf0, -1.0);
+  tile_gemm<PM>(Q0 + i0, M, T, v.R, X + i0 + (size_t)j0 * M, M, mr, nc, nf0, -1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * mr * (double)nc * nf0);
 }
 
@@ -713,7 +709,7 @@ __global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
 
 // L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R.
 // grid (tiles over r_old, tiles over rn, 2 * cnt); Lm zeroed beforehand
-template <bool OZ>
+template <int PM>
 __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   int t = blockIdx.z >> 1, side = blockIdx.z & 1;
   if (c.skip[t]) return;
@@ -724,14 +720,8 @@ __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   const double* Q = qbase(c, t, side, M);
   const double* B = side == 0 ? v.u(b) : v.v(b);
   double* Lm = c.Lm + ((size_t)t * 2 + side) * v.R * v.R;
-  if (OZ && ro - j0 > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
-    tile_gemm_64_oz<true>(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R,
-                          min(64, rn - i0), min(64, ro - j0), m, 1.0, oz_dyn);
-  } else {
-    tile_gemm_64_tn(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0,
-                    ro - j0, m, 1.0);
-  }
+  tile_gemm_tn<PM>(Q + (size_t)i0 * M, M, B + (size_t)j0 * M, M, Lm + i0 + (size_t)j0 * v.R, v.R, rn - i0, ro - j0,
+                   m, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, ro - j0) * m);
 }
 
@@ -775,7 +765,7 @@ __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
 // row side fill-ins: M2P_bq -> A_bq += U~^T M2P_bq ; P2P_bq -> P2L_bq = U~^T P2P_bq
 // (the P2L block is zero before b is eliminated).  grid (ns5 * tpc, tiles
 // over rn, cnt) with tpc column tiles per block.
-template <bool OZ>
+template <int PM>
 __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
   int s = blockIdx.x / tpc, tj = blockIdx.x % tpc, t = blockIdx.z;
   if (c.skip[t]) return;
@@ -794,15 +784,8 @@ __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
   bool elim = colour_of(q, v.d) < c.col;
   double* dst = elim ? v.ly(b, slot6(bc, q, v.d)) : v.lx(b, s);
   const double* Q = c.Q + ((size_t)t * 2) * v.M * v.M;
-  if (OZ && sw.cols - j0 > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
-    tile_gemm_64_oz<true>(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld,
-                          dst + i0 + (size_t)j0 * v.R, v.R, min(64, rn - i0), min(64, sw.cols - j0), sw.rows, 1.0,
-                          oz_dyn);
-  } else {
-    tile_gemm_64_tn(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld, dst + i0 + (size_t)j0 * v.R,
-                    v.R, rn - i0, sw.cols - j0, sw.rows, 1.0);
-  }
+  tile_gemm_tn<PM>(Q + (size_t)i0 * v.M, v.M, sw.src + (size_t)j0 * sw.ld, sw.ld, dst + i0 + (size_t)j0 * v.R, v.R,
+                   rn - i0, sw.cols - j0, sw.rows, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, sw.cols - j0) * sw.rows);
 }
 
@@ -904,7 +887,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
 // column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
 // (the M2P block into y_b is zero before b is eliminated).
 // grid (ns5 * tpr, tiles over rn, cnt) with tpr row tiles per block.
-template <bool OZ>
+template <int PM>
 __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
   int s = blockIdx.x / tpr, ti = blockIdx.x % tpr, t = blockIdx.z;
   if (c.skip[t]) return;
@@ -932,7 +915,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
     ldd = v.M;
   }
   const double* Q = qbase(c, t, 1, v.M);
-  tile_gemm<OZ>(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd,
+  tile_gemm<PM>(sw.src + i0, sw.ld, Q + (size_t)j0 * v.M, v.M, dst + i0 + (size_t)j0 * ldd, ldd,
                 min(64, sw.rows - i0), min(64, rn - j0), sw.cols, 1.0);
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, sw.rows - i0) * (double)min(64, rn - j0) * sw.cols);
 }
@@ -998,6 +981,7 @@ struct Elim {
   LuItem* lu;          // [cnt]
   SolveItem* sv;       // [cnt]
   double* colmax;      // [cnt][P]
+  int* err;            // device error word
 };
 
 // coupled rows / columns of every box of the colour and the LU / solve items
@@ -1147,9 +1131,9 @@ __device__ inline double* schur_target(const LV& v, int rbox, int rtype, int cty
 // elimination keeps: Piv and the Schur complement stay symmetric) the block
 // (j, i) is the transpose of (i, j): only i <= j is computed and each
 // off-diagonal tile is also stored transposed at its mirror.
-// OZ: the tile product on the tensor cores (tile_gemm_64_oz, FP64 precision,
-// OZ_SMEM bytes of dynamic shared memory) instead of FP64 FMAs.
-template <bool OZ>
+// PM: the tile product mode (dense.cuh): FP64 FMAs, the BF16 warp MMAs or
+// tcgen05 in FP64 precision, or FP32.
+template <int PM>
 __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   int t = blockIdx.z;
   int ri = blockIdx.y / tpb, ti = blockIdx.y % tpb;
@@ -1181,9 +1165,14 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   int sp = slot5(pc, bc, v.d);
   const double* A = R.type == 0 ? v.xx(R.box, sp) : v.lx(R.box, sp);
   int lda = R.type == 0 ? v.M : v.R;
-  if (OZ) {
+  if (PM == PM_TC05) {
+    extern __shared__ unsigned char ozs[];
+    tile_gemm_64_tc(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs, e.err);
+  } else if (PM == PM_OZ) {
     extern __shared__ unsigned char ozs[];
     tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
+  } else if (PM == PM_F32) {
+    tile_gemm_64<float>(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   } else {
     tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   }
@@ -1236,6 +1225,23 @@ __global__ void k_xoff(int nb, int d, const int* __restrict__ r, int* __restrict
 }  // namespace
 
 // ---------------------------------------------------------------------------
+
+// launch kernel template KERN in the product mode pm (PM_FMA, PM_OZ or
+// PM_F32), with the dynamic shared memory the mode needs
+#define AIFMM_LAUNCH_PM(pm, KERN, grid, ...)                                   \
+  do {                                                                         \
+    if ((pm) == PM_OZ)                                                         \
+      KERN<PM_OZ><<<(grid), 256, OZ_SMEM, st>>>(__VA_ARGS__);                  \
+    else if ((pm) == PM_F32)                                                   \
+      KERN<PM_F32><<<(grid), 256, 0, st>>>(__VA_ARGS__);                       \
+    else                                                                       \
+      KERN<PM_FMA><<<(grid), 256, 0, st>>>(__VA_ARGS__);                       \
+  } while (0)
+
+// product mode of the compress fills and projections, the Schur update
+// (unless tcgen05 is chosen there) and, with PM_F32, of the Z solve and the
+// pivot LU's trailing updates
+static int product_mode(const Handle& h) { return h.fp32 ? PM_F32 : h.fma_gemm ? PM_FMA : PM_OZ; }
 
 static int alloc_level(Handle& h, FacLevel& F) {
   const size_t nb = F.nb;
@@ -1403,6 +1409,7 @@ static int factor_level(Handle& h, int l) {
   LV v = view(h, F);
   const int ncol = ipow(3, d);
   int nws = ipow(5, d) - ipow(3, d);
+  const int pm = product_mode(h);
   DetailProf dp;
   dp.on = std::getenv("AIFMM_PROFILE_DETAIL") != nullptr;
   dp.st = st;
@@ -1487,13 +1494,8 @@ static int factor_level(Handle& h, int l) {
         const int ncx = what == 0 ? c.WC : F.M;
         const dim3 g1((ncx + 63) / 64, ptiles_r, cnt * nsides), g2((ncx + 63) / 64, (F.M + 63) / 64, cnt * nsides);
         dp.begin(phase == 1 ? "project_fill" : "project_basis");
-        if (h.fma_gemm) {
-          k_cmp_ptq<false><<<g1, 256, 0, st>>>(v, c, what);
-          k_cmp_pqt<false><<<g2, 256, 0, st>>>(v, c, what);
-        } else {
-          k_cmp_ptq<true><<<g1, 256, OZ_SMEM, st>>>(v, c, what);
-          k_cmp_pqt<true><<<g2, 256, OZ_SMEM, st>>>(v, c, what);
-        }
+        AIFMM_LAUNCH_PM(pm, k_cmp_ptq, g1, v, c, what);
+        AIFMM_LAUNCH_PM(pm, k_cmp_pqt, g2, v, c, what);
         h.nlaunch += 2;
         dp.end();
       }
@@ -1505,11 +1507,7 @@ static int factor_level(Handle& h, int l) {
     AIFMM_CUDA_TRY(h, cudaMemsetAsync(c.Lm, 0, sizeof(double) * (size_t)cnt * 2 * F.R * F.R, st));
     {
       const int rt = (F.R + 63) / 64;
-      if (h.fma_gemm) {
-        k_cmp_lmat<false><<<dim3(rt, rt, 2 * cnt), 256, 0, st>>>(v, c);
-      } else {
-        k_cmp_lmat<true><<<dim3(rt, rt, 2 * cnt), 256, OZ_SMEM, st>>>(v, c);
-      }
+      AIFMM_LAUNCH_PM(pm, k_cmp_lmat, dim3(rt, rt, 2 * cnt), v, c);
       ++h.nlaunch;
     }
     dp.end();
@@ -1518,11 +1516,7 @@ static int factor_level(Handle& h, int l) {
     dp.end();
     dp.begin("row_fill");
     const int tpc = (F.M + 63) / 64, rtl = (F.R + 63) / 64;
-    if (h.fma_gemm) {
-      k_cmp_row_fill<false><<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc);
-    } else {
-      k_cmp_row_fill<true><<<dim3(F.ns5 * tpc, rtl, cnt), 256, OZ_SMEM, st>>>(v, c, tpc);
-    }
+    AIFMM_LAUNCH_PM(pm, k_cmp_row_fill, dim3(F.ns5 * tpc, rtl, cnt), v, c, tpc);
     ++h.nlaunch;
     dp.end();
     dp.begin("row_done");
@@ -1532,11 +1526,7 @@ static int factor_level(Handle& h, int l) {
     k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     dp.begin("col_fill");
-    if (h.fma_gemm) {
-      k_cmp_col_fill<false><<<dim3(F.ns5 * tpc, rtl, cnt), 256, 0, st>>>(v, c, tpc);
-    } else {
-      k_cmp_col_fill<true><<<dim3(F.ns5 * tpc, rtl, cnt), 256, OZ_SMEM, st>>>(v, c, tpc);
-    }
+    AIFMM_LAUNCH_PM(pm, k_cmp_col_fill, dim3(F.ns5 * tpc, rtl, cnt), v, c, tpc);
     ++h.nlaunch;
     dp.end();
     dp.begin("col_done");
@@ -1555,6 +1545,7 @@ static int factor_level(Handle& h, int l) {
     e.lu = (LuItem*)hscratch(h, 29, sizeof(LuItem) * cnt);
     e.sv = (SolveItem*)hscratch(h, 30, sizeof(SolveItem) * cnt);
     e.colmax = (double*)hscratch(h, 31, sizeof(double) * (size_t)cnt * F.P);
+    e.err = h.derr;
     if (!e.rows || !e.cols || !eb || !e.Z || !e.lu || !e.sv || !e.colmax) return HOOM;
     e.nrow = eb;
     e.ncol = eb + cnt;
@@ -1577,7 +1568,11 @@ static int factor_level(Handle& h, int l) {
         k_lu_laswp<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
         k_lu_trsm<<<dim3((F.P + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
         int tiles = (F.P + 63) / 64;
-        k_lu_gemm<<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0); ++h.nlaunch;
+        if (pm == PM_F32)
+          k_lu_gemm<PM_F32><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+        else
+          k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+        ++h.nlaunch;
       }
     }
     k_piv_perm<<<(cnt + 127) / 128, 128, 0, st>>>(v, col, cnt); ++h.nlaunch;
@@ -1611,7 +1606,11 @@ static int factor_level(Handle& h, int l) {
         }
         ++h.nlaunch;
         if (k0 + TB < F.P) {
-          k_lus_update<1, false><<<dim3(ctiles, (F.P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0);
+          const dim3 g(ctiles, (F.P - k0 - TB + 63) / 64, cnt);
+          if (pm == PM_F32)
+            k_lus_update<1, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
+          else
+            k_lus_update<1, PM_FMA><<<g, 256, 0, st>>>(e.sv, k0);
           ++h.nlaunch;
         }
       }
@@ -1623,7 +1622,11 @@ static int factor_level(Handle& h, int l) {
         }
         ++h.nlaunch;
         if (k0 > 0) {
-          k_lus_update<0, false><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(e.sv, k0);
+          const dim3 g(ctiles, (k0 + 63) / 64, cnt);
+          if (pm == PM_F32)
+            k_lus_update<0, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
+          else
+            k_lus_update<0, PM_FMA><<<g, 256, 0, st>>>(e.sv, k0);
           ++h.nlaunch;
         }
       }
@@ -1633,10 +1636,12 @@ static int factor_level(Handle& h, int l) {
     int tpb = (F.M + 63) / 64;
     gt = new GroupTimer(h, Handle::G_SCHUR);
     dp.begin("schur");
-    if (h.fma_gemm) {
-      k_schur<false><<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, 0, st>>>(v, e, tpb, h.sym ? 1 : 0);
-    } else {
-      k_schur<true><<<dim3(MAXC * tpb, MAXC * tpb, cnt), 256, OZ_SMEM, st>>>(v, e, tpb, h.sym ? 1 : 0);
+    {
+      const dim3 g(MAXC * tpb, MAXC * tpb, cnt);
+      if (pm == PM_OZ && h.tc05)
+        k_schur<PM_TC05><<<g, 256, TC_SMEM, st>>>(v, e, tpb, h.sym ? 1 : 0);
+      else
+        AIFMM_LAUNCH_PM(pm, k_schur, g, v, e, tpb, h.sym ? 1 : 0);
     }
     ++h.nlaunch;
     dp.end();
@@ -1708,12 +1713,13 @@ int run_factor(Handle& h) {
   if (!h.dacc) h.dacc = hnew<double>(h, 4);
   if (!h.dacc) return HOOM;
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_schur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_lmat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_row_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_col_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_ptq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_pqt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_schur<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_schur<PM_TC05>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_lmat<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_row_fill<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_col_fill<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_ptq<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_pqt<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
 
   {
     // tallest LU panel kept in shared memory: (rows x 32) doubles within the
@@ -1777,7 +1783,7 @@ int run_factor(Handle& h) {
     k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
     k_lu_trsm<<<dim3((h.ntop + 3) / 4, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
-    k_lu_gemm<<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
+    k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
   }
   k_ipiv_perm<<<1, 1, 0, st>>>(h.top_ipiv, h.ntop, h.top_perm); ++h.nlaunch;
   h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;

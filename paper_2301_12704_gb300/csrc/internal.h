@@ -101,6 +101,8 @@ struct Handle {
   bool profile = false;
   bool sym = true;      // A = A^T exploited by the factorisation
   bool fma_gemm = false;   // Schur tiles on FP64 FMAs instead of the tensor-core emulation
+  bool tc05 = false;       // Schur tiles on tcgen05 (TMEM accumulators) instead of the warp MMAs
+  bool fp32 = false;       // FP32 products in the factorisation (preconditioner)
   enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_NG = 4 };
   double g_ms[G_NG] = {0, 0, 0, 0};
   double g_flops[G_NG] = {0, 0, 0, 0};

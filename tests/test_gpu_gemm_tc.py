@@ -73,3 +73,44 @@ def test_dgemm_tc_rejects_bad_arguments(A):
     import ctypes as C
     lib = A.lib()
     assert lib.aifmm_dgemm_tc(None, 1, None, 1, None, 1, 1, 1, 1, 1.0, None) == 1
+
+
+@pytest.mark.parametrize("m,n,k", [(64, 64, 64), (130, 77, 201), (1, 200, 5), (257, 129, 1000), (64, 64, 31)])
+def test_dgemm_tc05_matches_the_mma_tile(A, m, n, k):
+    """The tcgen05 tile (tensor-memory accumulators, integer fixed point
+    across K) has the FP64-size error of the warp-MMA tile relative to
+    |C| + |A||B|, and the two agree to that level."""
+    rng = np.random.default_rng(m * 5 + n * 11 + k)
+    a = rng.standard_normal((m, k))
+    b = rng.standard_normal((k, n))
+    if m > 2:
+        a[1, :] = 0.0
+    c = rng.standard_normal((m, n))
+    ref = _ref(a, b, c, -1.0)
+    scale = np.abs(c) + np.abs(a) @ np.abs(b)
+    cd = _cm(c)
+    A.aifmm_dgemm_tc(_cm(a), _cm(b), cd, -1.0, tcgen05=True)
+    got = cd.cpu().numpy()
+    err = float(np.max(np.abs(got - ref) / scale))
+    assert err <= 2.0 ** -48, err
+
+
+def test_dgemm_tc05_wide_dynamic_range(A):
+    """Rows and columns spanning many binades: the same per-chunk bound as
+    the warp-MMA tile, 2^-48 sum_k (max|A_i.| |B_kj| + |A_ik| max|B_.j|)
+    (chunks of 32 here, so the bound with chunk maxima of 64 holds)."""
+    rng = np.random.default_rng(5)
+    m, n, k = 96, 80, 300
+    a = rng.standard_normal((m, k))
+    b = rng.standard_normal((k, n))
+    a[:, ::7] *= 1e-9
+    b[::5, :] *= 1e6
+    c = np.zeros((m, n))
+    cd = _cm(c)
+    A.aifmm_dgemm_tc(_cm(a), _cm(b), cd, 1.0, tcgen05=True)
+    got = cd.cpu().numpy()
+    ref = _ref(a, b, c, 1.0)
+    ra = np.abs(a).max(axis=1, keepdims=True)
+    cb = np.abs(b).max(axis=0, keepdims=True)
+    bound = 2.0 ** -48 * (ra @ np.ones((1, k)) @ np.abs(b) + np.abs(a) @ np.ones((k, 1)) @ cb)
+    assert np.all(np.abs(got - ref) <= bound)

@@ -84,16 +84,17 @@ def _oracle_solution(w, pts, b):
     return _ORACLE_X[w.name]
 
 
-@pytest.mark.parametrize("symmetric,fma", [(True, False), (False, False), (True, True)],
-                         ids=["sym", "general", "sym-fp64fma"])
+@pytest.mark.parametrize("symmetric,mode", [(True, "mma"), (False, "mma"), (True, "fma"), (True, "tcgen05")],
+                         ids=["sym", "general", "sym-fp64fma", "sym-tcgen05"])
 @pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
-def test_factor_solve_matches_oracle(A, w, symmetric, fma):
-    """Both elimination modes, and the Schur tiles on the tensor cores or on
-    FP64 FMAs, against the oracle's general elimination: they differ from it
-    only by rounding and the RRQR cut-off, so the same 10 tol bound holds."""
+def test_factor_solve_matches_oracle(A, w, symmetric, mode):
+    """Both elimination modes, and the Schur tiles on the warp MMAs, on
+    tcgen05 or on FP64 FMAs, against the oracle's general elimination: they
+    differ from it only by rounding and the RRQR cut-off, so the same 10 tol
+    bound holds."""
     pts, b = W.points_and_rhs(w, nrhs=2)
     h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, symmetric=symmetric,
-                      fma_gemm=fma)
+                      fma_gemm=mode == "fma", tcgen05=mode == "tcgen05")
     A.aifmm_factor(h)
     x = A.aifmm_solve(h, b)
     xo, xd = _oracle_solution(w, pts, b)
