@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--batched", type=int, default=0,
+                   help="also run this many independent uneven problems (1 and 8 host threads)")
     p.add_argument("--mixed3d", type=int, default=0,
                    help="also run the 3D mixed-precision GMRES configuration at this many points")
     return p.parse_args()
@@ -155,35 +157,23 @@ def reference_arm(args, ws, rank):
     }), flush=True)
 
 
-def serve(A, w, pts, stream, dev, requests=64, seed=4):
-    """Solve requests against one resident factorisation: nrhs uniform in
-    1..32, b ~ N(0,1), host buffers in and out; latency = wall time of the
-    C-ABI call (copies included).  Sequential requests, no batching."""
-    import numpy as np
-    import torch
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, stream=stream.cuda_stream)
-    A.aifmm_factor(h)
-    rng = np.random.default_rng(seed)
-    reqs = []
-    for _ in range(requests):
-        k = int(rng.integers(1, 33))
-        reqs.append(np.asfortranarray(rng.standard_normal((w.n, k))))
-    for b in reqs[:3]:
-        A.aifmm_solve(h, b)
-    lat, cols = [], 0
-    for b in reqs:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        A.aifmm_solve(h, b)
-        lat.append(time.perf_counter() - t0)
-        cols += b.shape[1]
-    A.aifmm_destroy(h)
-    lat_ms = np.array(lat) * 1e3
-    tot = float(np.sum(lat))
-    return {"requests": requests, "nrhs": "uniform 1..32 (seed 4)", "solves_per_s": cols / tot,
-            "requests_per_s": requests / tot, "p50_ms": float(np.percentile(lat_ms, 50)),
-            "p99_ms": float(np.percentile(lat_ms, 99)),
-            "note": "sequential solve requests against one resident factorisation; host rhs in, host x out"}
+def serve(A, duration=8.0, rate=25.0, seed=4):
+    """The serving loop (paper_2301_12704_gb300.serve): Poisson arrivals of
+    factor requests (10%) and solve requests (nrhs 1..32) against resident
+    factorisations, continuous batching of the solves, memory admission
+    under a 150 GB cap.  Host arrays in and out; latency from arrival to the
+    result on the host."""
+    import workloads as W
+    from paper_2301_12704_gb300 import serve as S
+    trace = W.serving_trace(seed=seed, rate=rate, duration=duration)
+    reqs = S.requests_from_trace(trace)
+    srv = S.Server(cap_bytes=150e9, max_cols=64)
+    m = srv.run(reqs, timeout=600)
+    srv.close()
+    m["workload"] = (f"Poisson {rate:g} req/s for {duration:g} s (seed {seed}): 10% factor requests (2D log kernel, "
+                     "A_ii = N, N log-uniform 4,096..32,768, tol 1e-8, leaf 64), 90% solve requests (nrhs 1..32, "
+                     "b ~ N(0,1)) against one of the 4 latest factorisations; batches of up to 64 columns; cap 150 GB")
+    return m
 
 
 def gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-6, rtol=1e-10, fp32=False):
@@ -250,6 +240,23 @@ def mixed3d(A, dev, n=32768, rtol=1e-10):
             "ms_build": t[0], "ms_factor": t[1], "ms_gmres": t[2], "iterations": it, "relres_h2": rr,
             "residual_direct_sum": true, "levels": st["levels"], "max_rank": st["max_rank_factor"],
             "gb_resident": st["bytes_resident"] / 1e9, "points_per_s": n / ((t[1] + t[2]) / 1e3)}
+    return out
+
+
+def batched(A, count=256, workers=(1, 8)):
+    """Many independent GP-style problems of uneven size (Gaussian kernel,
+    length 0.1, + 1e-2 I on [0,1]^2, N log-uniform 2,048..32,768, seed 3,
+    tol 1e-10, leaf 64): factor + solve of all of them, with 1 and with
+    several host threads driving one handle and stream per problem;
+    points/s = total points / wall time."""
+    import workloads as W
+    from paper_2301_12704_gb300 import batch as B
+    probs = W.batched_problems(seed=3, count=count)
+    out = {"workload": f"{count} problems: Gaussian kernel exp(-r^2/0.1^2) + 1e-2 I on [0,1]^2, N log-uniform "
+                       "2,048..32,768 (seed 3), tol 1e-10, leaf 64, one rhs each; FP64"}
+    for k in workers:
+        _, m = B.factor_solve_many(probs, workers=k)
+        out[f"workers_{k}"] = m
     return out
 
 
@@ -388,9 +395,11 @@ def main():
                       "note": "wall time of aifmm_factor + aifmm_solve with host rhs in and host x out; "
                               "the host points enter through aifmm_build, which the metric excludes"}
     if not args.no_serve:
-        out["serve"] = serve(A, w, pts, stream, dev)
+        out["serve"] = serve(A)
         out["gmres_mode"] = gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-4)
         out["gmres_mode_fp32"] = gmres_mode(A, w, pts_d, b1_d, stream, ftol=1e-4, fp32=True)
+    if args.batched:
+        out["batched"] = batched(A, count=args.batched)
     if args.mixed3d:
         out["mixed3d"] = mixed3d(A, dev, n=args.mixed3d)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -81,3 +81,53 @@ def gauss2d(n: int, seed: int, leaf: int = 64, tol: float = 1e-10, nrhs: int = 1
 SMALL = log2d(4096, seed=0)
 BENCH = log2d(65536, seed=1)
 BENCH64 = log2d(65536, seed=1, nrhs=64)
+
+
+def serving_trace(seed: int = 4, rate: float = 50.0, duration: float = 8.0, frac_factor: float = 0.1,
+                  n_lo: int = 4096, n_hi: int = 32768, nrhs_max: int = 32, recent: int = 4,
+                  tol: float = 1e-8, leaf: int = 64):
+    """A request stream for the serving loop: Poisson arrivals (exponential
+    gaps at ``rate`` per second) over ``duration`` seconds; each request is a
+    factor request with probability ``frac_factor`` (the first one always
+    is), else a solve request.  Factor requests: 2D log kernel with
+    A_ii = N, N log-uniform in [n_lo, n_hi], points uniform in [-1,1]^2.
+    Solve requests: nrhs uniform in 1..nrhs_max, b ~ N(0,1), against one of
+    the ``recent`` most recently requested factorisations, uniformly.
+    Returns a list of dicts (kind, t, fid, and points or rhs)."""
+    rng = np.random.default_rng(seed)
+    out, t, fids, sizes = [], 0.0, [], {}
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        if not fids or rng.random() < frac_factor:
+            n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+            fid = len(fids)
+            fids.append(fid)
+            sizes[fid] = n
+            out.append({"kind": "factor", "t": t, "fid": fid, "points": rng.uniform(-1.0, 1.0, (n, 2)),
+                        "kernel": LOG2D, "diag": float(n), "tol": tol, "leaf": leaf})
+        else:
+            fid = fids[-1 - int(rng.integers(0, min(recent, len(fids))))]
+            k = int(rng.integers(1, nrhs_max + 1))
+            out.append({"kind": "solve", "t": t, "fid": fid,
+                        "rhs": np.asfortranarray(rng.standard_normal((k, sizes[fid])).T)})
+    return out
+
+
+def batched_problems(seed: int = 3, count: int = 256, n_lo: int = 2048, n_hi: int = 32768, tol: float = 1e-10,
+                     leaf: int = 64):
+    """Many independent GP-style problems of uneven size: N log-uniform in
+    [n_lo, n_hi] (one generator for all, seed ``seed``), points uniform in
+    [0,1]^2, A = exp(-|x-y|^2/0.1^2) + 1e-2 I, one right-hand side
+    b ~ N(0,1) each.  Returns a list of (Workload, points, rhs)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        w = Workload(f"gauss2d_batch{i}_N{n}", n, 2, 0.0, 1.0, seed, GAUSS, 1.0 + 1e-2, leaf, tol, 1,
+                     length=0.1)
+        pts = rng.uniform(0.0, 1.0, (n, 2))
+        b = np.asfortranarray(rng.standard_normal((n, 1)))
+        out.append((w, pts, b))
+    return out
