@@ -260,6 +260,24 @@ def batched(A, count=256, workers=(1, 8)):
     return out
 
 
+def max_over_ranks(vals, dev, ws):
+    """Element-wise maximum of per-rank timings over the process group
+    (every rank gets it); identity on one process."""
+    if ws <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([float(v) for v in vals], device=dev, dtype=torch.float64)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return [float(v) for v in x.tolist()]
+
+
+def replica_value(ws, n, steps, ms_max):
+    """Whole-job points/s of ws replicas, each factoring and solving steps
+    problems of n points: all points over the slowest rank's time."""
+    return ws * n * steps / (ms_max / 1e3)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -341,11 +359,8 @@ def main():
     ts64 = sum(t[3] for t in times)
     tstep = sum(sum(t) for t in times)
     fs_ms = tf + ts1
-    if ws > 1:
-        x = torch.tensor([fs_ms, tstep], device=dev, dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        fs_ms, tstep = float(x[0]), float(x[1])
-    value = ws * args.n * args.steps / (fs_ms / 1e3)
+    fs_ms, tstep = max_over_ranks([fs_ms, tstep], dev, ws)
+    value = replica_value(ws, args.n, args.steps, fs_ms)
 
     # dominant kernel group of the factorisation -> roofline (FP64 ALU bound)
     names = ["compress", "pivot_lu", "z_solve", "schur"]
