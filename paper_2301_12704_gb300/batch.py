@@ -20,17 +20,22 @@ def _one(points, kernel, diag, tol, leaf, length, rhs, fp32, factor_tol):
     t0 = time.perf_counter()
     h = aifmm_build(points, kernel, diag, tol, leaf, length=length, fp32=fp32, factor_tol=factor_tol)
     t1 = time.perf_counter()
-    aifmm_factor(h)
-    x = aifmm_solve(h, rhs)
+    try:
+        aifmm_factor(h)
+        x = aifmm_solve(h, rhs)
+    except Exception as e:         # e.g. a rank above the compiled-in capacity: reported, not fatal
+        aifmm_destroy(h)
+        return None, t1 - t0, time.perf_counter() - t1, 0.0, 0, repr(e)
     t2 = time.perf_counter()
     st = aifmm_stats(h)
     aifmm_destroy(h)
-    return x, t1 - t0, t2 - t1, st["bytes_resident"], st["max_rank_factor"]
+    return x, t1 - t0, t2 - t1, st["bytes_resident"], st["max_rank_factor"], None
 
 
 def factor_solve_many(problems, workers: int = 8, fp32: bool = False, factor_tol: float = 0.0):
     """problems: iterable of (Workload, points, rhs) (workloads.batched_problems).
-    Returns (solutions in order, metrics)."""
+    Returns (solutions in order, None for a problem whose factorisation
+    failed, and metrics; points/s counts the solved problems only)."""
     problems = list(problems)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
@@ -38,9 +43,11 @@ def factor_solve_many(problems, workers: int = 8, fp32: bool = False, factor_tol
                 for (w, p, b) in problems]
         res = [f.result() for f in futs]
     wall = time.perf_counter() - t0
-    npts = sum(len(p) for (_, p, _) in problems)
+    ok = [r[5] is None for r in res]
+    npts = sum(len(p) for (_, p, _), g in zip(problems, ok) if g)
     return [r[0] for r in res], {
-        "problems": len(problems), "points": npts, "workers": workers, "wall_s": wall,
+        "problems": len(problems), "failed": len(ok) - sum(ok),
+        "errors": sorted({r[5] for r in res if r[5]})[:3], "points": npts, "workers": workers, "wall_s": wall,
         "points_per_s": npts / wall, "sum_build_s": sum(r[1] for r in res),
         "sum_factor_solve_s": sum(r[2] for r in res), "max_gb": max(r[3] for r in res) / 1e9,
         "max_rank": max(r[4] for r in res)}

@@ -202,13 +202,15 @@ struct Cmp {
   double* Q;           // [cnt][2][M*M]  bases U~ (side 0) and V~ (side 1)
   double* cn;          // [cnt][2][WC]   residual column norms^2
   int* nc;             // [cnt][2] gathered columns
+  int* boff;           // [cnt][2][ns5] column offset in W of each pending block, -1: none
   int* rk;             // [cnt][2] own ranks
   int* rn;             // [cnt] equalised rank
   int* rold;           // [cnt] rank before compression
   int* skip;           // [cnt] 1 if nothing is pending
   double* Lm;          // [cnt][2][R*R] L_b (side 0), R_b (side 1), ld R
   double* T;           // [cnt][2][R*WC] Q0^T X of the projections, ld R
-  double* tau;         // [cnt][2] RRQR threshold eps * max_j ||F_j|| of the fill-in columns
+  double* tau;         // [cnt][2] max_j ||F_j||^2 of the fill-in columns (bit pattern, atomicMax);
+                       // the RRQR threshold is eps * sqrt of it
   int phase;           // k_cmp_qrcp: 1 = QR of the basis columns, 2 = QRCP of the projected fill-ins
   int ccap;            // k_cmp_qrcp: column capacity of the phase (shared-memory norms)
   double eps;
@@ -275,47 +277,78 @@ __device__ __noinline__ WsBlk ws_block(const LV v, int b, int s, int side, int c
   return w;
 }
 
+// the pending blocks of each box side and their column offsets in W after
+// the basis (stencil-slot order), the gathered column count and r_b; the
+// threshold accumulator cleared.  One thread per (box, side).
+__global__ void k_cmp_list(LV v, Cmp c, int nsides) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= c.cnt * nsides) return;
+  const int t = x / nsides, side = x % nsides;
+  const int b = cbox(c, v, t);
+  const int rb = v.r[b];
+  int* off = c.boff + ((size_t)t * 2 + side) * v.ns5;
+  int o = rb;
+  for (int sl = 0; sl < v.ns5; ++sl) {
+    WsBlk w = ws_block(v, b, sl, side, c.col);
+    off[sl] = w.ok ? o : -1;
+    if (w.ok) o += side == 0 ? w.cols : w.rows;
+  }
+  c.nc[t * 2 + side] = o;
+  if (side == 0) c.rold[t] = rb;
+  c.tau[t * 2 + side] = 0.0;
+}
+
 // gather [U_b | row fill-ins] (side 0) and [V_b | column fill-ins^T] (side 1)
-// grid (cnt, 2)
-__global__ void k_cmp_gather(LV v, Cmp c) {
-  __shared__ WsBlk list[128];
-  __shared__ int offs[128];
-  __shared__ int nlist, total;
-  int t = blockIdx.x, side = blockIdx.y;
-  int b = cbox(c, v, t);
-  int mb = v.m[b], rb = v.r[b];
+// into W; blockIdx.y = 0 copies the basis, blockIdx.y = 1 + s the pending
+// block of stencil slot s, and takes the largest squared norm of its columns
+// into the threshold accumulator (non-negative doubles order as their bit
+// patterns).  grid (cnt * sides, ns5 + 1)
+__global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
+  __shared__ WsBlk sw;
+  __shared__ double shm[8];
+  const int t = blockIdx.x / nsides, side = blockIdx.x % nsides;
+  const int b = cbox(c, v, t);
+  const int mb = v.m[b], rb = c.rold[t];
   double* W = c.W + ((size_t)t * 2 + side) * v.M * c.WC;
-  if (threadIdx.x == 0) {
-    int nl = 0, off = rb;
-    for (int s = 0; s < v.ns5 && nl < 128; ++s) {
-      WsBlk w = ws_block(v, b, s, side, c.col);
-      if (!w.ok) continue;
-      list[nl] = w;
-      offs[nl] = off;
-      off += side == 0 ? w.cols : w.rows;
-      ++nl;
+  if (blockIdx.y == 0) {
+    const double* base = side == 0 ? v.u(b) : v.v(b);
+    for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
+      int i = e % mb, j = e / mb;
+      W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
     }
-    nlist = nl;
-    total = off;
+    return;
+  }
+  const int sl = blockIdx.y - 1;
+  const int off = c.boff[((size_t)t * 2 + side) * v.ns5 + sl];
+  if (off < 0) return;
+  if (threadIdx.x == 0) sw = ws_block(v, b, sl, side, c.col);
+  __syncthreads();
+  const WsBlk w = sw;
+  for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
+    int i = e % w.rows, j = e / w.rows;
+    if (side == 0) W[i + (size_t)(off + j) * v.M] = w.src[i + (size_t)j * w.ld];
+    else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
   }
   __syncthreads();
-  const double* base = side == 0 ? v.u(b) : v.v(b);
-  for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
-    int i = e % mb, j = e / mb;
-    W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
-  }
-  for (int k = 0; k < nlist; ++k) {
-    WsBlk w = list[k];
-    int off = offs[k];
-    for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
-      int i = e % w.rows, j = e / w.rows;
-      if (side == 0) W[i + (size_t)(off + j) * v.M] = w.src[i + (size_t)j * w.ld];
-      else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
+  // largest squared column norm of the copied columns (m_b rows each)
+  const int ncol = side == 0 ? w.cols : w.rows;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double mx = 0.0;
+  for (int j = wp; j < ncol; j += 8) {
+    double a = 0.0;
+    for (int i = lane; i < mb; i += 32) {
+      const double x = W[i + (size_t)(off + j) * v.M];
+      a += x * x;
     }
+    mx = fmax(mx, warp_sum(a));
   }
+  if (lane == 0) shm[wp] = mx;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    c.nc[t * 2 + side] = total;
-    if (side == 0) c.rold[t] = rb;
+    double a = 0.0;
+    for (int q = 0; q < 8; ++q) a = fmax(a, shm[q]);
+    atomicMax(reinterpret_cast<unsigned long long*>(c.tau + t * 2 + side), (unsigned long long)__double_as_longlong(a));
+    atomicAdd(c.flops, 2.0 * mb * (double)ncol);
   }
 }
 
@@ -337,7 +370,7 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 //   phase 2  Householder QR with column pivoting of the projected F: the
 //            largest residual column while its norm exceeds
 //            tau = eps * max_j ||F_j|| (norms of the fill-ins before the
-//            projection, k_cmp_tau); Q' = Q[:, nf:rank], then made orthogonal
+//            projection, k_cmp_gather); Q' = Q[:, nf:rank], then made orthogonal
 //            to Q0 once more (the projection leaves Q0 components of size
 //            u ||F_j|| / |R_kk|).
 // Produces Q[:, :rank] explicitly, rank = nf + (phase-2 columns).
@@ -397,7 +430,7 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
     acc = warp_sum(acc);
     if (lane == 0) cnl[jl] = cref[jl] = acc;
   }
-  const double tau = c.tau[t * 2 + side];
+  const double tau = c.eps * sqrt(c.tau[t * 2 + side]);
   __syncthreads();
   const int kmax = min(m - coff, n);     // the projected columns lie in m - nf0 dimensions
   int k = 0;
@@ -564,34 +597,6 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
     double f = 2.0 * m * (n - nf);
     for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
     atomicAdd(c.flops, f);
-  }
-}
-
-// RRQR threshold of each box side: tau = eps * max_j ||F_j|| over the
-// gathered fill-in columns W[:, nf0:nc] (before any projection); grid
-// (cnt * sides), 256 threads
-__global__ void __launch_bounds__(256) k_cmp_tau(LV v, Cmp c) {
-  __shared__ double shm[8];
-  const int nsd = c.sym ? 1 : 2;
-  const int t = blockIdx.x / nsd, side = blockIdx.x % nsd;
-  if (c.skip[t]) return;
-  const int b = cbox(c, v, t);
-  const int m = v.m[b], M = v.M, nf0 = c.rold[t], n = c.nc[t * 2 + side];
-  const double* W = c.W + ((size_t)t * 2 + side) * M * c.WC;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double mx = 0.0;
-  for (int j = nf0 + w; j < n; j += 8) {
-    double a = 0.0;
-    for (int i = lane; i < m; i += 32) a += W[i + (size_t)j * M] * W[i + (size_t)j * M];
-    mx = fmax(mx, warp_sum(a));
-  }
-  if (lane == 0) shm[w] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int q = 0; q < 8; ++q) a = fmax(a, shm[q]);
-    c.tau[t * 2 + side] = c.eps * sqrt(a);
-    atomicAdd(c.flops, 2.0 * m * (double)(n - nf0));
   }
 }
 
@@ -791,50 +796,46 @@ __global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
 
 // after the row side: clear the redirected fill-in blocks and their flags
 // (a P2P_bq leaves a pending P2L_bq for q's column side), U_b := U~,
-// r_b := rn ; grid cnt
+// r_b := rn.  grid (ns5 + 1, cnt): blockIdx.x = s < ns5 the block of stencil
+// slot s (the list made by k_cmp_list before any flag changed), ns5 the basis
 __global__ void k_cmp_row_done(LV v, Cmp c) {
-  __shared__ WsBlk list[128];
-  __shared__ int slots[128];
-  __shared__ int nl;
-  int t = blockIdx.x;
+  __shared__ WsBlk sw;
+  const int sl = blockIdx.x, t = blockIdx.y;
   if (c.skip[t]) return;
-  int b = cbox(c, v, t);
-  int bc[3], q[3];
-  morton_coords(b, v.d, v.l, bc);
+  const int b = cbox(c, v, t);
   const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (sl == v.ns5) {
+    const double* Q = c.Q + ((size_t)t * 2) * M * M;
+    for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
+      int i = e % m, j = e / m;
+      v.u(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
+    }
+    return;
+  }
+  if (c.boff[((size_t)t * 2) * v.ns5 + sl] < 0) return;
+  if (threadIdx.x == 0) sw = ws_block(v, b, sl, 0, c.col);
+  __syncthreads();
+  const WsBlk w = sw;
+  double* src = const_cast<double*>(w.src);
+  for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
+    int i = e % w.rows, j = e / w.rows;
+    src[i + (size_t)j * w.ld] = 0.0;
+  }
   if (threadIdx.x == 0) {
-    int n = 0;
-    for (int s = 0; s < v.ns5 && n < 128; ++s) {
-      WsBlk w = ws_block(v, b, s, 0, c.col);
-      if (!w.ok) continue;
-      list[n] = w;
-      slots[n++] = s;
-    }
-    nl = n;
+    int bc[3], q[3];
+    morton_coords(b, v.d, v.l, bc);
+    slot5_coords(bc, sl, v.d, q);
+    unsigned* f = v.flag + (size_t)b * v.ns5 + sl;
+    atomicAnd(f, ~1u);
+    if (colour_of(q, v.d) > c.col) atomicOr(f, 2u);   // a new P2L_bq waits for q's column side
   }
-  __syncthreads();
-  for (int k = 0; k < nl; ++k) {
-    double* src = const_cast<double*>(list[k].src);
-    for (int e = threadIdx.x; e < list[k].rows * list[k].cols; e += blockDim.x) {
-      int i = e % list[k].rows, j = e / list[k].rows;
-      src[i + (size_t)j * list[k].ld] = 0.0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < nl; ++k) {
-      int s = slots[k];
-      slot5_coords(bc, s, v.d, q);
-      unsigned* f = v.flag + (size_t)b * v.ns5 + s;
-      atomicAnd(f, ~1u);
-      if (colour_of(q, v.d) > c.col) atomicOr(f, 2u);   // a new P2L_bq waits for q's column side
-    }
-  const double* Q = c.Q + ((size_t)t * 2) * M * M;
-  for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
-    int i = e % m, j = e / m;
-    v.u(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
-  }
-  if (threadIdx.x == 0) v.r[b] = rn;
+}
+
+// the new rank of every box of the colour, after the row side's blocks are done
+__global__ void k_cmp_set_rank(LV v, Cmp c) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= c.cnt || c.skip[t]) return;
+  v.r[cbox(c, v, t)] = c.rn[t];
 }
 
 // column side: every block of the multipole column of b is multiplied by
@@ -921,49 +922,41 @@ __global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
 }
 
 // after the column side: clear the redirected blocks, the consumed P2L flags
-// (a P2P_qb became a pending M2P_qb, which keeps bit 0), V_b := V~ ; grid cnt
+// (a P2P_qb became a pending M2P_qb, which keeps bit 0), V_b := V~.
+// grid (ns5 + 1, cnt) as k_cmp_row_done; the pending column-side block of
+// slot s is found from the partner's flag, which only this CTA changes
 __global__ void k_cmp_col_done(LV v, Cmp c) {
-  __shared__ WsBlk list[128];
-  __shared__ int slots[128];
-  __shared__ int nl;
-  int t = blockIdx.x;
+  __shared__ WsBlk sw;
+  const int sl = blockIdx.x, t = blockIdx.y;
   if (c.skip[t]) return;
-  int b = cbox(c, v, t);
-  int bc[3], q[3];
-  morton_coords(b, v.d, v.l, bc);
+  const int b = cbox(c, v, t);
   const int m = v.m[b], M = v.M, rn = c.rn[t];
+  if (sl == v.ns5) {
+    const double* Q = qbase(c, t, 1, M);
+    for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
+      int i = e % m, j = e / m;
+      v.v(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
+    }
+    return;
+  }
+  if (threadIdx.x == 0) sw = ws_block(v, b, sl, 1, c.col);
+  __syncthreads();
+  const WsBlk w = sw;
+  if (!w.ok) return;
+  double* src = const_cast<double*>(w.src);
+  for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
+    int i = e % w.rows, j = e / w.rows;
+    src[i + (size_t)j * w.ld] = 0.0;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int n = 0;
-    for (int s = 0; s < v.ns5 && n < 128; ++s) {
-      WsBlk w = ws_block(v, b, s, 1, c.col);
-      if (!w.ok) continue;
-      list[n] = w;
-      slots[n++] = s;
+    int bc[3], q[3];
+    morton_coords(b, v.d, v.l, bc);
+    slot5_coords(bc, sl, v.d, q);
+    if (colour_of(q, v.d) < c.col) {
+      int qb = morton_key(q, v.d, v.l);
+      atomicAnd(v.flag + (size_t)qb * v.ns5 + slot5(q, bc, v.d), ~2u);
     }
-    nl = n;
-  }
-  __syncthreads();
-  for (int k = 0; k < nl; ++k) {
-    double* src = const_cast<double*>(list[k].src);
-    for (int e = threadIdx.x; e < list[k].rows * list[k].cols; e += blockDim.x) {
-      int i = e % list[k].rows, j = e / list[k].rows;
-      src[i + (size_t)j * list[k].ld] = 0.0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < nl; ++k) {
-      int s = slots[k];
-      slot5_coords(bc, s, v.d, q);
-      if (colour_of(q, v.d) < c.col) {
-        int qb = morton_key(q, v.d, v.l);
-        atomicAnd(v.flag + (size_t)qb * v.ns5 + slot5(q, bc, v.d), ~2u);
-      }
-    }
-  const double* Q = qbase(c, t, 1, M);
-  for (int e = threadIdx.x; e < m * rn; e += blockDim.x) {
-    int i = e % m, j = e / m;
-    v.v(b)[i + (size_t)j * M] = Q[i + (size_t)j * M];
   }
 }
 
@@ -1065,14 +1058,17 @@ __global__ void k_piv_perm(LV v, int col, int cnt) {
 }
 
 // Piv = [[K_bb, U_b], [V_b^T, 0]] into the LU storage; grid cnt
+// grid (cnt, PB_SLICES): slice y takes the columns j = y, y + PB_SLICES, ...
+constexpr int PB_SLICES = 16;
 __global__ void k_piv_build(LV v, Elim e) {
   int t = blockIdx.x;
   int b = colour_box(e.col, t, v.d, v.l);
   const int m = v.m[b], r = v.r[b], n = m + r, P = v.P, M = v.M;
   double* A = v.lu(b);
   const double* K = v.xx(b, v.centre5());
-  for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
-    int i = x % n, j = x / n;
+  const int nj = n > (int)blockIdx.y ? (n - (int)blockIdx.y + PB_SLICES - 1) / PB_SLICES : 0;
+  for (int x = threadIdx.x; x < n * nj; x += blockDim.x) {
+    int i = x % n, j = (int)blockIdx.y + PB_SLICES * (x / n);
     double val;
     if (i < m && j < m) val = K[i + (size_t)j * M];
     else if (i < m) val = v.u(b)[i + (size_t)(j - m) * M];
@@ -1085,6 +1081,8 @@ __global__ void k_piv_build(LV v, Elim e) {
 // B = A[pivot rows, coupled columns]: [c_C; 0] for x_q / y_q, [0; -I] for y_b,
 // stored with the pivot LU's row interchanges already applied (row i of Z
 // holds row pp[i] of B)
+// grid (MAXC, cnt, ZB_SLICES): slice z takes the columns j = z, z + ZB_SLICES, ...
+constexpr int ZB_SLICES = 4;
 __global__ void k_z_build(LV v, Elim e) {
   int t = blockIdx.y, ci = blockIdx.x;
   if (ci >= e.ncol[t]) return;
@@ -1095,9 +1093,11 @@ __global__ void k_z_build(LV v, Elim e) {
   Coupled C = e.cols[(size_t)t * MAXC + ci];
   double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)C.off * P;
   const int* pr = v.pp(b);
+  const int z = blockIdx.z;
+  const int nj = C.size > z ? (C.size - z + ZB_SLICES - 1) / ZB_SLICES : 0;
   if (C.type == 2) {
-    for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
-      int i = x % n, j = x / n;
+    for (int x = threadIdx.x; x < n * nj; x += blockDim.x) {
+      int i = x % n, j = z + ZB_SLICES * (x / n);
       Z[i + (size_t)j * P] = (pr[i] - m == j) ? -1.0 : 0.0;
     }
     return;
@@ -1105,8 +1105,8 @@ __global__ void k_z_build(LV v, Elim e) {
   morton_coords(C.box, v.d, v.l, qc);
   int s = slot5(bc, qc, v.d);
   const double* src = C.type == 0 ? v.xx(b, s) : v.xy(b, s);
-  for (int x = threadIdx.x; x < n * C.size; x += blockDim.x) {
-    int i = x % n, j = x / n;
+  for (int x = threadIdx.x; x < n * nj; x += blockDim.x) {
+    int i = x % n, j = z + ZB_SLICES * (x / n);
     int r = pr[i];
     Z[i + (size_t)j * P] = r < m ? src[r + (size_t)j * v.M] : 0.0;
   }
@@ -1434,7 +1434,8 @@ static int factor_level(Handle& h, int l) {
     c.Lm = (double*)hscratch(h, 24, sizeof(double) * (size_t)cnt * 2 * F.R * F.R);
     c.T = (double*)hscratch(h, 32, sizeof(double) * (size_t)cnt * 2 * F.R * c.WC);
     c.tau = (double*)hscratch(h, 33, sizeof(double) * (size_t)cnt * 2);
-    if (!c.W || !c.Q || !c.cn || !ib || !c.Lm || !c.T || !c.tau) return HOOM;
+    c.boff = (int*)hscratch(h, 34, sizeof(int) * (size_t)cnt * 2 * F.ns5);
+    if (!c.W || !c.Q || !c.cn || !ib || !c.Lm || !c.T || !c.tau || !c.boff) return HOOM;
     c.nc = ib;
     c.rk = ib + 2 * cnt;
     c.rn = ib + 4 * cnt;
@@ -1442,14 +1443,11 @@ static int factor_level(Handle& h, int l) {
     c.skip = ib + 6 * cnt;
     GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
     dp.begin("gather");
-    k_cmp_gather<<<dim3(cnt, nsides), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_list<<<(cnt * nsides + 127) / 128, 128, 0, st>>>(v, c, nsides); ++h.nlaunch;
+    k_cmp_gather<<<dim3(cnt * nsides, F.ns5 + 1), 256, 0, st>>>(v, c, nsides); ++h.nlaunch;
     dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
     {
-      // threshold from the fill-in columns as gathered
-      dp.begin("tau");
-      k_cmp_tau<<<cnt * nsides, 256, 0, st>>>(v, c); ++h.nlaunch;
-      dp.end();
       // phase 1 (QR of U_b) in clusters of two CTAs; phase 2 (QRCP of the
       // projected fill-ins) in clusters of qc CTAs, qc so that the colour's
       // clusters give about two CTAs per SM
@@ -1520,7 +1518,8 @@ static int factor_level(Handle& h, int l) {
     ++h.nlaunch;
     dp.end();
     dp.begin("row_done");
-    k_cmp_row_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_row_done<<<dim3(F.ns5 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_set_rank<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     dp.begin("col_transform");
     k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
@@ -1530,7 +1529,7 @@ static int factor_level(Handle& h, int l) {
     ++h.nlaunch;
     dp.end();
     dp.begin("col_done");
-    k_cmp_col_done<<<cnt, 256, 0, st>>>(v, c); ++h.nlaunch;
+    k_cmp_col_done<<<dim3(F.ns5 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
     delete gt;
     // ---- pivot LU
@@ -1553,7 +1552,7 @@ static int factor_level(Handle& h, int l) {
     k_coupled<<<(cnt + 127) / 128, 128, 0, st>>>(v, e); ++h.nlaunch;
     gt = new GroupTimer(h, Handle::G_PIVLU);
     dp.begin("piv_build");
-    k_piv_build<<<cnt, 256, 0, st>>>(v, e); ++h.nlaunch;
+    k_piv_build<<<dim3(cnt, PB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
     dp.end();
     k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P); ++h.nlaunch;
     dp.begin("lu");
@@ -1581,7 +1580,7 @@ static int factor_level(Handle& h, int l) {
     // ---- Z = Piv^-1 B and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
     dp.begin("z_build");
-    k_z_build<<<dim3(MAXC, cnt), 256, 0, st>>>(v, e); ++h.nlaunch;
+    k_z_build<<<dim3(MAXC, cnt, ZB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
     dp.end();
     {
       // blocked LU solve of Z (interchanges applied by k_z_build): unit-lower
