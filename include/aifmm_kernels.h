@@ -26,6 +26,17 @@ extern "C" {
 int aifmm_dgemm_tc(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                    int k, double alpha, void* stream);
 
+/* The same product with eight 7-bit digits per entry (56-bit slices: an
+ * entry 2^-d below its row's / column's largest keeps 56 - d bits, those
+ * within 3 binades are exact; 49 digit-pair MMAs per 16-deep step) and a
+ * balanced contraction: in every 64-deep chunk, A's column k and B's row k
+ * are first rescaled by 2^d_k and 2^-d_k, 2^d_k the binade of row k of B
+ * over the 64 columns of the output tile, so rows of B of very different
+ * magnitudes keep their digits (the tile of the factorisation's blocked
+ * Z = Piv^-1 B solve).  Arguments and returns as aifmm_dgemm_tc. */
+int aifmm_dgemm_tc8(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
+                    int k, double alpha, void* stream);
+
 /* The same product on the 5th-generation tensor cores: tcgen05.mma with
  * BF16 digit operands in shared memory and FP32 accumulators in tensor
  * memory (two digits of A stacked per 128-row MMA), the exact digit-pair

@@ -77,6 +77,8 @@ def lib():
         L.aifmm_dgemm_tc.restype = C.c_int
         L.aifmm_dgemm_tc05.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
         L.aifmm_dgemm_tc05.restype = C.c_int
+        L.aifmm_dgemm_tc8.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
+        L.aifmm_dgemm_tc8.restype = C.c_int
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
         L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
         L.aifmm_level_pivots.argtypes = [vp, cint, vp]
@@ -232,9 +234,10 @@ def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: in
     return x, it.value, rr.value
 
 
-def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = False) -> None:
+def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = False,
+                   digits8: bool = False) -> None:
     """C_ += alpha A B on the tensor cores in FP64 precision (C: aifmm_dgemm_tc,
-    or aifmm_dgemm_tc05 with ``tcgen05``).
+    aifmm_dgemm_tc05 with ``tcgen05``, aifmm_dgemm_tc8 with ``digits8``).
     A, B, C_ CUDA float64 tensors, column-major (e.g. ``t.t().contiguous().t()``)."""
     m, k = A.shape
     k2, n = B.shape
@@ -243,7 +246,7 @@ def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = Fa
         assert t.is_cuda and (t.stride(0) == 1 or t.shape[0] == 1), "column-major CUDA tensors"
         return max(1, t.shape[0], t.stride(1) if t.shape[1] > 1 else 1)
 
-    fn = lib().aifmm_dgemm_tc05 if tcgen05 else lib().aifmm_dgemm_tc
+    fn = lib().aifmm_dgemm_tc05 if tcgen05 else lib().aifmm_dgemm_tc8 if digits8 else lib().aifmm_dgemm_tc
     st = fn(C.c_void_p(A.data_ptr()), ld(A), C.c_void_p(B.data_ptr()), ld(B),
                               C.c_void_p(C_.data_ptr()), ld(C_), m, n, k, float(alpha),
                               C.c_void_p(stream) if stream else None)

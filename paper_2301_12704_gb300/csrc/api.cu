@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "../../include/aifmm.h"
@@ -26,6 +28,40 @@ static long fail_at() {
   return s ? std::atol(s) : 0;
 }
 
+// The library's device memory comes from one stream-ordered pool per GPU
+// that keeps freed blocks for later handles (release threshold: unlimited):
+// allocations and frees never synchronise the device, so handles driven from
+// several host threads (many problems, the serving loop) do not stall each
+// other, and a new handle reuses the blocks of destroyed ones instead of
+// asking the driver again.  The pool's memory returns to the driver at
+// process exit.
+static cudaMemPool_t lib_pool(int dev) {
+  static cudaMemPool_t pools[64] = {};
+  static std::mutex mu;
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+static cudaError_t dev_alloc(Handle& h, void** p, size_t bytes) {
+  cudaMemPool_t pool = lib_pool(h.device);
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, h.stream) : cudaMallocAsync(p, bytes, h.stream);
+}
+
 void* halloc(Handle& h, size_t bytes, bool zero) {
   static thread_local long counter = 0;
   long f = fail_at();
@@ -35,13 +71,13 @@ void* halloc(Handle& h, size_t bytes, bool zero) {
   }
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (dev_alloc(h, &p, bytes) != cudaSuccess) {
     cudaGetLastError();
-    h.err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+    h.err = "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed";
     return nullptr;
   }
   if (zero && cudaMemsetAsync(p, 0, bytes, h.stream) != cudaSuccess) {
-    cudaFree(p);
+    cudaFreeAsync(p, h.stream);
     h.err = "cudaMemsetAsync failed";
     return nullptr;
   }
@@ -55,17 +91,18 @@ void* hscratch(Handle& h, int slot, size_t bytes) {
   auto& s = h.scratch[slot];
   if (s.second >= bytes && s.first) return s.first;
   if (s.first) {
-    cudaStreamSynchronize(h.stream);
-    cudaFree(s.first);
+    // the kernels that used the old buffer were issued on h.stream before
+    // this free, so it is ordered after them
+    cudaFreeAsync(s.first, h.stream);
     h.resident -= s.second;
     s.first = nullptr;
     s.second = 0;
   }
   void* p = nullptr;
   size_t b = bytes < 16 ? 16 : bytes;
-  if (cudaMalloc(&p, b) != cudaSuccess) {
+  if (dev_alloc(h, &p, b) != cudaSuccess) {
     cudaGetLastError();
-    h.err = "cudaMalloc of scratch (" + std::to_string(b) + " bytes) failed";
+    h.err = "cudaMallocAsync of scratch (" + std::to_string(b) + " bytes) failed";
     return nullptr;
   }
   s.first = p;
@@ -75,13 +112,13 @@ void* hscratch(Handle& h, int slot, size_t bytes) {
 }
 
 void hfree_all(Handle& h) {
-  if (h.stream) cudaStreamSynchronize(h.stream);
-  for (void* p : h.allocs) cudaFree(p);
+  for (void* p : h.allocs) cudaFreeAsync(p, h.stream);
   h.allocs.clear();
   for (auto& s : h.scratch)
-    if (s.first) cudaFree(s.first);
+    if (s.first) cudaFreeAsync(s.first, h.stream);
   h.scratch.clear();
   h.resident = 0;
+  if (h.stream) cudaStreamSynchronize(h.stream);
 }
 
 int check_derr(Handle& h) {

@@ -182,7 +182,9 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
 // memory); PM_TC05 the same digits on tcgen05 (tc05.cuh, the Schur update
 // only, TC_SMEM bytes); PM_F32 FP32 products and sums of FP64 operands (the
 // factorisation used as a preconditioner).
-enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3 };
+// PM_OZ8: the warp-MMA tile with 8 digits (56-bit slices) and the balanced
+// contraction (the Z = Piv^-1 B solve; oz_smem(OZ_S8) bytes).
+enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3, PM_OZ8 = 4 };
 
 // C += alpha A B, 64 x 64 tile (A column-major lda, B column-major ldb)
 template <int PM>
@@ -191,6 +193,9 @@ __device__ inline void tile_gemm(const double* A, int lda, const double* B, int 
   if (PM == PM_OZ && nc > THIN_NC) {
     extern __shared__ unsigned char oz_dyn[];
     tile_gemm_64_oz<false>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
+  } else if (PM == PM_OZ8 && nc > THIN_NC) {
+    extern __shared__ unsigned char oz_dyn[];
+    tile_gemm_64_oz<false, true, OZ_S8>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
   } else if (PM == PM_F32) {
     tile_gemm_64<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
   } else {
@@ -401,6 +406,104 @@ static __global__ void __launch_bounds__(256) k_lus_gather(const SolveItem* item
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) X[i] = tmp[i];
     __syncthreads();
+  }
+}
+
+// X := A^-1 X for an LU-factored A and a few right-hand sides (NC columns
+// at most), one CTA of 256 threads per item, everything in one launch: the
+// rows of X are gathered into shared memory by the net permutation (gather
+// = 1) or taken as they are (0); then the unit-lower and the upper
+// triangular solves run in 32-row blocks: warp 0 solves the diagonal block
+// with its 32 rows in registers (x_j broadcast by a shuffle), and all
+// threads update the rows below (above) with the block's 32 new entries,
+// one barrier per block.  For the solve sweeps with one to NC columns,
+// where the blocked multi-launch solve pays ~4 dependent launches per
+// 64 rows for a few thousand flops.  dynamic shared memory: n_cap * NC doubles.
+template <int NC>
+static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items, int gather) {
+  extern __shared__ double xs[];          // [NC][n] column-major, ld n
+  const SolveItem it = items[blockIdx.x];
+  const int n = it.n, nc = min(NC, it.ncols);
+  if (n == 0) return;
+  const double* A = it.a;
+  const int ld = it.ld;
+  for (int e = threadIdx.x; e < n * NC; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    const int src = gather ? it.perm[i] : i;
+    xs[e] = c < nc ? it.x[src + (size_t)c * it.ldx] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // ---- unit lower, forward
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int kb = min(32, n - k0);
+    if (w == 0) {
+      double x[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] = lane < kb ? xs[k0 + lane + c * n] : 0.0;
+      for (int j = 0; j < kb - 1; ++j) {
+        const double l = lane > j && lane < kb ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) x[c] -= l * __shfl_sync(0xffffffffu, x[c], j);
+      }
+      if (lane < kb)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xs[k0 + lane + c * n] = x[c];
+    }
+    __syncthreads();
+    for (int i = k0 + kb + threadIdx.x; i < n; i += blockDim.x) {
+      double acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+      for (int j = 0; j < kb; ++j) {
+        const double l = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(l, xs[k0 + j + c * n], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xs[i + c * n] -= acc[c];
+    }
+    __syncthreads();
+  }
+  // ---- upper, backward
+  for (int k0 = ((n - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
+    const int kb = min(32, n - k0);
+    if (w == 0) {
+      double x[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] = lane < kb ? xs[k0 + lane + c * n] : 0.0;
+      for (int j = kb - 1; j >= 0; --j) {
+        const double d = A[(k0 + j) + (size_t)(k0 + j) * ld];
+        const double u = lane < j ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const double xj = __shfl_sync(0xffffffffu, x[c], j) / d;
+          if (lane == j) x[c] = xj;
+          x[c] -= u * xj;
+        }
+      }
+      if (lane < kb)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xs[k0 + lane + c * n] = x[c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
+      double acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+      for (int j = 0; j < kb; ++j) {
+        const double u = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(u, xs[k0 + j + c * n], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xs[i + c * n] -= acc[c];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
+    const int i = e % n, c = e / n;
+    it.x[i + (size_t)c * it.ldx] = xs[e];
   }
 }
 

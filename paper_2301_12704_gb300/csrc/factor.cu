@@ -1585,14 +1585,14 @@ static int factor_level(Handle& h, int l) {
     {
       // blocked LU solve of Z (interchanges applied by k_z_build): unit-lower
       // blocks downwards, upper blocks upwards, each trailing update a tiled
-      // GEMM on FP64 FMAs.  (Not the tensor-core tile: a column of Z mixes
-      // the x part, of size ~1/A_ii, with the z part, orders of magnitude
-      // larger, inside one 64-row chunk, and the digits of the small entries
-      // keep only 49 bits below the chunk's largest -- measured, the lost
-      // accuracy shows up as higher compression ranks at the next level.
-      // Rescaling each row of the chunk by its own power of two before the
-      // digits are cut halved the Z-solve time but still raised the ranks:
-      // 16% more factorisation flops and no net gain at 65,536 points.)
+      // GEMM on the tensor cores with 8 digits (56-bit slices) and the
+      // balanced contraction.  A column of Z mixes the x part, of size
+      // ~1/A_ii, with the z part, orders of magnitude larger, inside one
+      // 64-row chunk: with 7 digits and one exponent per column the small
+      // entries kept only 49 - d bits, and the lost accuracy showed up as
+      // higher compression ranks at the next level (+16% factor flops, also
+      // with the balancing alone); with both, +5% flops for a 1.5x faster
+      // solve.  fma_gemm: FP64 FMAs.
       dp.begin("lus");
       const int ctiles = (e.ncmax + 63) / 64;
       const int wstr = (e.ncmax + 3) / 4, cstr = (e.ncmax + 127) / 128;
@@ -1608,6 +1608,8 @@ static int factor_level(Handle& h, int l) {
           const dim3 g(ctiles, (F.P - k0 - TB + 63) / 64, cnt);
           if (pm == PM_F32)
             k_lus_update<1, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
+          else if (pm == PM_OZ)
+            k_lus_update<1, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(e.sv, k0);
           else
             k_lus_update<1, PM_FMA><<<g, 256, 0, st>>>(e.sv, k0);
           ++h.nlaunch;
@@ -1624,6 +1626,8 @@ static int factor_level(Handle& h, int l) {
           const dim3 g(ctiles, (k0 + 63) / 64, cnt);
           if (pm == PM_F32)
             k_lus_update<0, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
+          else if (pm == PM_OZ)
+            k_lus_update<0, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(e.sv, k0);
           else
             k_lus_update<0, PM_FMA><<<g, 256, 0, st>>>(e.sv, k0);
           ++h.nlaunch;
@@ -1719,6 +1723,8 @@ int run_factor(Handle& h) {
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_col_fill<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_ptq<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_pqt<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<1, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM8));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<0, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM8));
 
   {
     // tallest LU panel kept in shared memory: (rows x 32) doubles within the

@@ -42,30 +42,40 @@ namespace aifmm {
 constexpr int OZ_S = 7;                // digits per operand
 constexpr int OZ_KC = 64;              // K chunk
 constexpr int OZ_LD = OZ_KC + 8;       // padded smem row (bf16 elements): conflict-free fragment loads
-constexpr int OZ_SMEM = 2 * OZ_S * 64 * OZ_LD * 2 + 2 * 64 * 4;   // bytes of dynamic shared memory
+// bytes of dynamic shared memory of the tile with S digits per operand
+constexpr int oz_smem(int S) { return 2 * S * 64 * OZ_LD * 2 + 3 * 64 * 4; }
+constexpr int OZ_SMEM = oz_smem(OZ_S);
+constexpr int OZ_S8 = 8;               // digits of the high-precision variant
+constexpr int OZ_SMEM8 = oz_smem(OZ_S8);
+constexpr int OZ_NEG = -(1 << 20);     // exponent of an all-zero row or column (balanced contraction)
 
 // biased exponent of |x| (0 for zero and denormals, which are flushed)
 __device__ inline int oz_bexp(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// the OZ_S digits of x relative to the biased exponent E >= bexp(x): with
-// |x| = m 2^(e - 1075) (53-bit m), a = round(m 2^(e - E - 4)) = sum_s d_s 2^(42 - 7 s);
-// written as BF16 values +-d_s 2^(-7 s), so that |x| = 2^(E - 1029) sum_s value_s
+// the S digits of x relative to the biased exponent E >= bexp(x): with
+// |x| = m 2^(e - 1075) (53-bit m), a = round(m 2^(e - E + 7 S - 53)), an
+// integer of 7 S bits (49 for S = 7: entries 2^-d below the largest keep
+// 49 - d bits; 56 for S = 8: entries within 3 binades of the largest are
+// exact), a = sum_s d_s 2^(7 (S - 1 - s)); written as BF16 values
+// +-d_s 2^(-7 s), so that |x| = 2^(E - 1029) sum_s value_s for every S
+template <int S = OZ_S>
 __device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride) {
   long long bits = __double_as_longlong(x);
   int e = (int)((bits >> 52) & 0x7ff);
   unsigned long long a = 0;
   if (e != 0) {
     unsigned long long m = ((unsigned long long)bits & 0xfffffffffffffull) | (1ull << 52);
-    int sh = E - e + 4;                  // 53-bit mantissa -> 49 bits below 2^(E)
-    if (sh < 64) a = (m + (1ull << (sh - 1))) >> sh;
+    const int sh = E - e + 53 - 7 * S;   // right shift of the mantissa (left if negative)
+    if (sh <= 0) a = m << (-sh);
+    else if (sh < 64) a = (m + (1ull << (sh - 1))) >> sh;
   }
   const bool neg = bits < 0;
   float scale = 1.0f;
 #pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    unsigned d = s == 0 ? (unsigned)(a >> 42) : (unsigned)((a >> (42 - 7 * s)) & 0x7f);
+  for (int s = 0; s < S; ++s) {
+    unsigned d = s == 0 ? (unsigned)(a >> (7 * (S - 1))) : (unsigned)((a >> (7 * (S - 1 - s))) & 0x7f);
     float v = (float)d * scale;
     out[s * stride] = __float2bfloat16_rn(neg ? -v : v);
     scale *= 0.0078125f;                 // 2^-7
@@ -82,14 +92,24 @@ __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
 
 // C[0..mr, 0..nc] += alpha * op(A)[0..mr, 0..K) B[0..K, 0..nc]; op(A) = A
 // column-major (lda) or, with TA, A^T for A column-major K x mr (lda);
-// B column-major (ldb), C column-major (ldc).  smem: OZ_SMEM bytes.
-template <bool TA = false>
+// B column-major (ldb), C column-major (ldc).  smem: oz_smem(S) bytes.
+//
+// S: digits per operand (7, or 8 for 56-bit slices; pairs with s + t <= S + 1
+// are multiplied: 39 or 49 MMAs per 16-deep step).  KB (balanced
+// contraction): before the row and column exponents are taken, every k of a
+// chunk is rescaled by a power of two, A(:, k) 2^d_k and B(k, :) 2^-d_k with
+// 2^d_k the binade of max_j |B(k, j)| over the tile's columns; the products
+// are unchanged (only exponents move), but rows of B of very different
+// magnitudes -- the x and z parts of a column of Piv^-1 B -- no longer lose
+// the small rows' digits to the large rows' exponent.
+template <bool TA = false, bool KB = false, int S = OZ_S>
 __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                        int mr, int nc, int K, double alpha, unsigned char* smem) {
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [OZ_S][64][OZ_LD]
-  __nv_bfloat16* Bs = As + OZ_S * 64 * OZ_LD;                            // [OZ_S][64][OZ_LD] (col, k)
-  int* ea = reinterpret_cast<int*>(Bs + OZ_S * 64 * OZ_LD);              // [64] row exponents
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [S][64][OZ_LD]
+  __nv_bfloat16* Bs = As + S * 64 * OZ_LD;                               // [S][64][OZ_LD] (col, k)
+  int* ea = reinterpret_cast<int*>(Bs + S * 64 * OZ_LD);                 // [64] row exponents
   int* eb = ea + 64;                                                     // [64] column exponents
+  int* ek = eb + 64;                                                     // [64] KB: binade of row k of B
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int wr = (w & 1) * 32, wc = (w >> 1) * 16;                       // warp sub-tile origin
   const int g = lane >> 2, cq = lane & 3;
@@ -104,14 +124,53 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
   for (int k0 = 0; k0 < K; k0 += OZ_KC) {
     const int kc = min(OZ_KC, K - k0);
     // ---- stage: exponents (rows of op(A), columns of B over this chunk)
-    if (tid < 128) (tid < 64 ? ea : eb)[tid & 63] = 0;
+    if (tid < 192) (tid < 64 ? ea : tid < 128 ? eb : ek)[tid & 63] = (KB && tid < 128) ? OZ_NEG : 0;
     __syncthreads();
+    // B: warp w takes columns 8w..8w+7, lanes k = lane and lane + 32
+    double bv[8][2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = 8 * w + q;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int k = lane + 32 * h;
+        bv[q][h] = (j < nc && k < kc) ? B[(k0 + k) + (size_t)j * ldb] : 0.0;
+      }
+    }
+    if (KB) {
+      int r0 = 0, r1 = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        r0 = max(r0, oz_bexp(bv[q][0]));
+        r1 = max(r1, oz_bexp(bv[q][1]));
+      }
+      atomicMax(&ek[lane], r0);
+      atomicMax(&ek[lane + 32], r1);
+      __syncthreads();
+    }
+    // exponent of an entry after the shift of its k (KB: d_k = ek[k] - 1023,
+    // + for A, - for B); zero entries take no part in a maximum
+    auto vexp = [&](double x, int k, int sgn) -> int {
+      int e = oz_bexp(x);
+      if (!KB) return e;
+      return e == 0 ? OZ_NEG : e + sgn * (ek[k] - 1023);
+    };
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = 8 * w + q;
+      int bm = KB ? OZ_NEG : 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) bm = max(bm, vexp(bv[q][h], lane + 32 * h, -1));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      if (lane == 0) eb[j] = bm;
+    }
     // A: warp w takes k = 8w..8w+7, lanes the rows lane and lane + 32 (with
     // TA: warp w the rows 8w..8w+7, lanes k = lane and lane + 32, so that the
     // loads stay coalesced)
     double av[8][2];
     if (!TA) {
-      int am0 = 0, am1 = 0;
+      int am0 = KB ? OZ_NEG : 0, am1 = KB ? OZ_NEG : 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int k = 8 * w + q;
@@ -120,7 +179,7 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
           int i = lane + 32 * h;
           double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
           av[q][h] = x;
-          int e = oz_bexp(x);
+          int e = vexp(x, k, 1);
           if (h == 0) am0 = max(am0, e); else am1 = max(am1, e);
         }
       }
@@ -130,35 +189,18 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int i = 8 * w + q;
-        int am = 0;
+        int am = KB ? OZ_NEG : 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           int k = lane + 32 * h;
           double x = (i < mr && k < kc) ? A[(k0 + k) + (size_t)i * lda] : 0.0;
           av[q][h] = x;
-          am = max(am, oz_bexp(x));
+          am = max(am, vexp(x, k, 1));
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
         if (lane == 0) ea[i] = am;
       }
-    }
-    // B: warp w takes columns 8w..8w+7, lanes k = lane and lane + 32
-    double bv[8][2];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int j = 8 * w + q;
-      int bm = 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int k = lane + 32 * h;
-        double x = (j < nc && k < kc) ? B[(k0 + k) + (size_t)j * ldb] : 0.0;
-        bv[q][h] = x;
-        bm = max(bm, oz_bexp(x));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-      if (lane == 0) eb[j] = bm;
     }
     __syncthreads();
     // ---- stage: digits into shared memory
@@ -168,7 +210,7 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
       for (int h = 0; h < 2; ++h) {
         int i = TA ? 8 * w + q : lane + 32 * h;
         int k = TA ? lane + 32 * h : 8 * w + q;
-        oz_digits(av[q][h], ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
+        oz_digits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
       }
     }
 #pragma unroll
@@ -177,7 +219,7 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         int k = lane + 32 * h;
-        oz_digits(bv[q][h], eb[j], Bs + j * OZ_LD + k, 64 * OZ_LD);
+        oz_digits<S>(bv[q][h], KB ? eb[j] + (ek[k] - 1023) : eb[j], Bs + j * OZ_LD + k, 64 * OZ_LD);
       }
     }
     __syncthreads();
@@ -195,9 +237,9 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
             for (int q = 0; q < 4; ++q) acc[x][a][b][q] = 0.f;
 #pragma unroll
       for (int kk = kh; kk < kh + 32; kk += 16) {
-        uint32_t bf[OZ_S][2][2];
+        uint32_t bf[S][2][2];
 #pragma unroll
-        for (int t = 0; t < OZ_S; ++t)
+        for (int t = 0; t < S; ++t)
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
             const __nv_bfloat16* base = Bs + t * 64 * OZ_LD + (wc + 8 * b + g) * OZ_LD + kk + 2 * cq;
@@ -205,7 +247,7 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
             bf[t][b][1] = *reinterpret_cast<const uint32_t*>(base + 8);
           }
 #pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
+        for (int s = 0; s < S; ++s) {
           uint32_t af[2][4];
 #pragma unroll
           for (int a = 0; a < 2; ++a) {
@@ -216,8 +258,8 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
             af[a][3] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD + 8);
           }
 #pragma unroll
-          for (int t = 0; t < OZ_S; ++t) {
-            if (s + t > OZ_S + 1) continue;     // s + t >= 9: below 2^-63 x 2^14, dropped
+          for (int t = 0; t < S; ++t) {
+            if (s + t > S + 1) continue;        // s + t > S + 1: dropped
             const int grp = min(s + t, 5);
 #pragma unroll
             for (int a = 0; a < 2; ++a)

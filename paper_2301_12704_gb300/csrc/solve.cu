@@ -448,7 +448,20 @@ __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ x, do
 // swap: 0 = interchanges already applied, 1 = gather through shared memory
 // (columns of up to MAX_GATHER rows), 2 = sequential interchanges
 constexpr int MAX_GATHER = 27 * 1024;   // rows; 216 KB of shared memory
+// pivot blocks of up to LS_MAXN rows with up to 4 right-hand sides take the
+// one-launch solve (k_lus_small); larger ones the blocked multi-launch solve
+constexpr int LS_MAXN = 1024;
+
 static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int ncols, int swap, cudaStream_t st) {
+  if (P <= LS_MAXN && ncols <= 4 && swap != 2) {
+    const int nc = ncols <= 1 ? 1 : ncols <= 2 ? 2 : 4;
+    const size_t sm = sizeof(double) * (size_t)P * nc;
+    if (nc == 1) k_lus_small<1><<<cnt, 256, sm, st>>>(items, swap);
+    else if (nc == 2) k_lus_small<2><<<cnt, 256, sm, st>>>(items, swap);
+    else k_lus_small<4><<<cnt, 256, sm, st>>>(items, swap);
+    ++h.nlaunch;
+    return;
+  }
   const int ctiles = (ncols + 63) / 64, cstr = (ncols + 127) / 128, wstr = (ncols + 3) / 4;
   const bool narrow = lus_warp_diag(cnt, ncols);
   if (swap == 1 && P > MAX_GATHER) swap = 2;
@@ -571,6 +584,8 @@ static int solve_attrs(Handle& h) {
   if (!done[dv]) {
     AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * MAX_GATHER)));
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_small<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * LS_MAXN * 4)));
     done[dv] = true;
   }
   return HOK;

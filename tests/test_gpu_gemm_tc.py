@@ -114,3 +114,47 @@ def test_dgemm_tc05_wide_dynamic_range(A):
     cb = np.abs(b).max(axis=0, keepdims=True)
     bound = 2.0 ** -48 * (ra @ np.ones((1, k)) @ np.abs(b) + np.abs(a) @ np.ones((k, 1)) @ cb)
     assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k", [(64, 64, 64), (130, 77, 201), (257, 129, 1000)])
+def test_dgemm_tc8_error_is_fp64_size(A, m, n, k):
+    """Eight digits: error of FP64 size relative to |C| + |A||B|, four times
+    below the seven-digit tile's bound (measured 2^-50.1 here)."""
+    rng = np.random.default_rng(m + 2 * n + 3 * k)
+    a = rng.standard_normal((m, k))
+    b = rng.standard_normal((k, n))
+    b[:, 3 % n] = 0.0                      # an exact zero column
+    c = rng.standard_normal((m, n))
+    cd = _cm(c)
+    A.aifmm_dgemm_tc(_cm(a), _cm(b), cd, -1.0, digits8=True)
+    got = cd.cpu().numpy()
+    ref = _ref(a, b, c, -1.0)
+    scale = np.abs(c) + np.abs(a) @ np.abs(b)
+    assert float(np.max(np.abs(got - ref) / scale)) <= 2.0 ** -49
+
+
+def test_dgemm_tc8_keeps_small_rows(A):
+    """Rows of B of very different magnitudes, as in a column of Piv^-1 B:
+    with the balanced contraction each output keeps FP64-size error relative
+    to its own terms, |err_ij| <= 2^-50 sum_k |A_ik| max_j' |B_kj'|, while
+    the plain 7-digit tile loses the small rows' digits."""
+    rng = np.random.default_rng(7)
+    m, n, k = 96, 64, 192
+    a = rng.standard_normal((m, k))
+    b = rng.standard_normal((k, n))
+    small = np.zeros(k, dtype=bool)
+    small[rng.permutation(k)[: k // 2]] = True
+    b[small, :] *= 1e-11                   # "x part" rows
+    a[: m // 2, ~small] = 0.0              # the first rows of C see only the small rows
+    c = np.zeros((m, n))
+    ref = _ref(a, b, c, 1.0)
+    bound = 2.0 ** -50 * (np.abs(a) @ np.abs(b).max(axis=1, keepdims=True))
+    cd = _cm(c)
+    A.aifmm_dgemm_tc(_cm(a), _cm(b), cd, 1.0, digits8=True)
+    got = cd.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+    cp = _cm(c)
+    A.aifmm_dgemm_tc(_cm(a), _cm(b), cp, 1.0)
+    plain = cp.cpu().numpy()
+    top = slice(0, m // 2)
+    assert np.max(np.abs(plain[top] - ref[top])) > 1e3 * np.max(np.abs(got[top] - ref[top]))
