@@ -183,7 +183,8 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
 // only, TC_SMEM bytes); PM_F32 FP32 products and sums of FP64 operands (the
 // factorisation used as a preconditioner).
 // PM_OZ8: the warp-MMA tile with 8 digits (56-bit slices) and the balanced
-// contraction (the Z = Piv^-1 B solve; oz_smem(OZ_S8) bytes).
+// contraction (the Z = Piv^-1 B solve and the pivot LU's trailing updates,
+// whose operands mix entries of very different sizes; oz_smem(OZ_S8) bytes).
 enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3, PM_OZ8 = 4 };
 
 // C += alpha A B, 64 x 64 tile (A column-major lda, B column-major ldb)
@@ -203,7 +204,7 @@ __device__ inline void tile_gemm(const double* A, int lda, const double* B, int 
   }
 }
 
-// A22 -= L21 U12 ; grid (coltiles, rowtiles, items); PM_FMA or PM_F32
+// A22 -= L21 U12 ; grid (coltiles, rowtiles, items); PM_FMA, PM_OZ8 or PM_F32
 template <int PM = PM_FMA>
 static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int k0) {
   LuItem it = items[blockIdx.z];

@@ -1171,6 +1171,7 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   } else if (PM == PM_OZ) {
     extern __shared__ unsigned char ozs[];
     tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
+
   } else if (PM == PM_F32) {
     tile_gemm_64<float>(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   } else {
@@ -1569,6 +1570,8 @@ static int factor_level(Handle& h, int l) {
         int tiles = (F.P + 63) / 64;
         if (pm == PM_F32)
           k_lu_gemm<PM_F32><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+        else if (pm == PM_OZ)
+          k_lu_gemm<PM_OZ8><<<dim3(tiles, tiles, cnt), 256, OZ_SMEM8, st>>>(e.lu, k0);
         else
           k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         ++h.nlaunch;
@@ -1724,6 +1727,7 @@ int run_factor(Handle& h) {
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_ptq<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_pqt<PM_OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<1, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM8));
+  AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lu_gemm<PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM8));
   AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<0, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM8));
 
   {
