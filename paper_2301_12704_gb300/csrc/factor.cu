@@ -730,10 +730,42 @@ __global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
   if (threadIdx.x == 0) atomicAdd(c.flops, 2.0 * min(64, rn - i0) * (double)min(64, ro - j0) * m);
 }
 
+constexpr int TR_CG = 4;   // columns (rows) per pass of the transforms
+
+// blk[0..rn, 0..ncols) := L blk[0..ro, 0..ncols) in place (L rn x ro, ld ldl;
+// blk ld ldb), TR_CG columns at a time through shared memory; each output is
+// the same p-ordered sum as one column at a time
+__device__ inline void transform_cols(double* blk, int ldb, int ncols, const double* L, int ldl, int rn, int ro,
+                                      double (*col)[1024]) {
+  for (int j0 = 0; j0 < ncols; j0 += TR_CG) {
+    const int nj = min(TR_CG, ncols - j0);
+    for (int e = threadIdx.x; e < TR_CG * ro; e += blockDim.x) {
+      const int u = e / ro, i = e % ro;
+      col[u][i] = u < nj ? blk[i + (size_t)(j0 + u) * ldb] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rn; i += blockDim.x) {
+      double acc[TR_CG];
+#pragma unroll
+      for (int u = 0; u < TR_CG; ++u) acc[u] = 0.0;
+      for (int p = 0; p < ro; ++p) {
+        const double l = L[i + (size_t)p * ldl];
+#pragma unroll
+        for (int u = 0; u < TR_CG; ++u) acc[u] += l * col[u][p];
+      }
+#pragma unroll
+      for (int u = 0; u < TR_CG; ++u)
+        if (u < nj) blk[i + (size_t)(j0 + u) * ldb] = acc[u];
+    }
+    __syncthreads();
+  }
+}
+
 // row side: every block of the locals row of b is multiplied by L_b
 // (the other-M2L and L2L updates); grid (ns6 + 1, cnt)
+// (TR_CG columns per pass, so that L_b is read once per TR_CG columns)
 __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
-  __shared__ double col[1024];
+  __shared__ double col[TR_CG][1024];
   int s = blockIdx.x, t = blockIdx.y;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -754,17 +786,7 @@ __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
     blk = v.ud(b);
     ncols = v.Rp;  // all parent columns (zeros beyond the parent's rank)
   }
-  for (int j = 0; j < ncols; ++j) {
-    double* cj = blk + (size_t)j * v.R;
-    for (int i = threadIdx.x; i < ro; i += blockDim.x) col[i] = cj[i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < rn; i += blockDim.x) {
-      double acc = 0.0;
-      for (int p = 0; p < ro; ++p) acc += Lm[i + (size_t)p * v.R] * col[p];
-      cj[i] = acc;
-    }
-    __syncthreads();
-  }
+  transform_cols(blk, v.R, ncols, Lm, v.R, rn, ro, col);
 }
 
 // row side fill-ins: M2P_bq -> A_bq += U~^T M2P_bq ; P2P_bq -> P2L_bq = U~^T P2P_bq
@@ -841,7 +863,7 @@ __global__ void k_cmp_set_rank(LV v, Cmp c) {
 // column side: every block of the multipole column of b is multiplied by
 // R_b^T (other-M2L and M2M updates); grid (ns6 + 1, cnt)
 __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
-  __shared__ double row[1024];
+  __shared__ double row[TR_CG][1024];
   int s = blockIdx.x, t = blockIdx.y;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -856,32 +878,34 @@ __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
     int db = morton_key(q, v.d, v.l);
     int sd = slot6(q, bc, v.d);
     double* blk = v.ly(db, sd);
-    int nrows = v.r[db];
-    for (int i = 0; i < nrows; ++i) {
-      for (int p = threadIdx.x; p < ro; p += blockDim.x) row[p] = blk[i + (size_t)p * v.R];
+    const int nrows = v.r[db];
+    // blk[0..nrows, 0..rn) := blk[.., 0..ro) R_b^T, TR_CG rows at a time
+    for (int i0 = 0; i0 < nrows; i0 += TR_CG) {
+      const int ni = min(TR_CG, nrows - i0);
+      for (int e = threadIdx.x; e < TR_CG * ro; e += blockDim.x) {
+        const int u = e / ro, p = e % ro;
+        row[u][p] = u < ni ? blk[(i0 + u) + (size_t)p * v.R] : 0.0;
+      }
       __syncthreads();
       for (int j = threadIdx.x; j < rn; j += blockDim.x) {
-        double acc = 0.0;
-        for (int p = 0; p < ro; ++p) acc += row[p] * Rm[j + (size_t)p * v.R];
-        blk[i + (size_t)j * v.R] = acc;
+        double acc[TR_CG];
+#pragma unroll
+        for (int u = 0; u < TR_CG; ++u) acc[u] = 0.0;
+        for (int p = 0; p < ro; ++p) {
+          const double r = Rm[j + (size_t)p * v.R];
+#pragma unroll
+          for (int u = 0; u < TR_CG; ++u) acc[u] += row[u][p] * r;
+        }
+#pragma unroll
+        for (int u = 0; u < TR_CG; ++u)
+          if (u < ni) blk[(i0 + u) + (size_t)j * v.R] = acc[u];
       }
       __syncthreads();
     }
   } else {
     if (v.l < 3) return;
     // V^dag_b (V form, r_old x rp) := R_b V^dag_b ; column-wise
-    double* blk = v.vd(b);
-    for (int j = 0; j < v.Rp; ++j) {
-      double* cj = blk + (size_t)j * v.R;
-      for (int i = threadIdx.x; i < ro; i += blockDim.x) row[i] = cj[i];
-      __syncthreads();
-      for (int i = threadIdx.x; i < rn; i += blockDim.x) {
-        double acc = 0.0;
-        for (int p = 0; p < ro; ++p) acc += Rm[i + (size_t)p * v.R] * row[p];
-        cj[i] = acc;
-      }
-      __syncthreads();
-    }
+    transform_cols(v.vd(b), v.R, v.Rp, Rm, v.R, rn, ro, row);
   }
 }
 
@@ -1152,7 +1176,8 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   morton_coords(C.box, v.d, v.l, qc);
   const double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)(C.off + j0) * P;
   int ldt;
-  double* T = schur_target(v, R.box, R.type, C.type, pc, qc, ldt) + i0 + (size_t)j0 * ldt;
+  double* T = schur_target(v, R.box, R.type, C.type, pc, qc, ldt);   // sets ldt
+  T += i0 + (size_t)j0 * ldt;
   int mr = min(64, R.size - i0), nc = min(64, C.size - j0);
   if (R.type == 2) {
     // (Lc_b, C) += Z[m + i, C]
@@ -1186,7 +1211,8 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
     // mirror: row entity of C, column entity of R (R is never Lc_b here)
     __syncthreads();
     int ldm;
-    double* Tm = schur_target(v, C.box, C.type, R.type, qc, pc, ldm) + j0 + (size_t)i0 * ldm;
+    double* Tm = schur_target(v, C.box, C.type, R.type, qc, pc, ldm);   // sets ldm
+    Tm += j0 + (size_t)i0 * ldm;
     for (int x = threadIdx.x; x < mr * nc; x += blockDim.x) {
       int j = x % nc, i = x / nc;
       Tm[j + (size_t)i * ldm] = T[i + (size_t)j * ldt];
