@@ -17,54 +17,6 @@ struct LuItem {
 
 constexpr int LU_NB = 32;
 
-// panel k0..k0+NB-1: pivot search, full-row interchange, scaling, rank-1
-// updates inside the panel.  One block per item.
-static __global__ void __launch_bounds__(256) k_lu_panel(const LuItem* items, int k0, int* err) {
-  __shared__ double shv[32];
-  __shared__ int shi[32];
-  LuItem it = items[blockIdx.x];
-  int n = it.n;
-  if (k0 >= n) return;
-  double* A = it.a;
-  const int ld = it.ld;
-  int kend = min(n, k0 + LU_NB);
-  for (int j = k0; j < kend; ++j) {
-    ArgMax best;
-    best.v = -1.0;
-    best.i = -1;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      ArgMax c;
-      c.v = fabs(A[i + (size_t)j * ld]);
-      c.i = i;
-      best = amax_pick(best, c);
-    }
-    best = block_amax(best, shv, shi);
-    int p = best.i;
-    double cm = it.colmax ? it.colmax[j] : 0.0;
-    if (!(best.v > 1e-14 * cm) || !(best.v > 0.0)) {
-      if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
-      return;
-    }
-    if (threadIdx.x == 0) it.ipiv[j] = p;
-    if (p != j)
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double t = A[j + (size_t)c * ld];
-        A[j + (size_t)c * ld] = A[p + (size_t)c * ld];
-        A[p + (size_t)c * ld] = t;
-      }
-    __syncthreads();
-    double piv = A[j + (size_t)j * ld];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (size_t)j * ld] /= piv;
-    __syncthreads();
-    int w = kend - j - 1, h = n - j - 1;
-    for (int e = threadIdx.x; e < w * h; e += blockDim.x) {
-      int i = j + 1 + e % h, c = j + 1 + e / h;
-      A[i + (size_t)c * ld] -= A[i + (size_t)j * ld] * A[j + (size_t)c * ld];
-    }
-    __syncthreads();
-  }
-}
-
 // U12 = L11^-1 A12 for the columns right of the panel: one warp per column,
 // lane i holding row k0 + i, x_j broadcast with a shuffle (lane-dense FP64;
 // see k_lus_diag_w).  grid (column groups of 4, items), 128 threads
@@ -218,9 +170,8 @@ static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int
                 n - i0, n - j0, kend - k0, -1.0);
 }
 
-// X := A^-1 X for an LU-factored A (ipiv interchanges, unit L, U) on a strip
-// of up to 32 right-hand-side columns; grid (strips, items).  X column-major
-// with leading dimension ldx, ncols columns, per item.
+// X := A^-1 X for an LU-factored A (ipiv interchanges, unit L, U), per item;
+// X column-major with leading dimension ldx, ncols columns.
 struct SolveItem {
   const double* a;
   const int* ipiv;
@@ -229,46 +180,6 @@ struct SolveItem {
   int ldx, ncols;
   const int* perm;   // net row permutation of ipiv (solve sweeps only), or null
 };
-
-static __global__ void __launch_bounds__(256) k_lu_solve_strip(const SolveItem* items) {
-  SolveItem it = items[blockIdx.y];
-  int c0 = blockIdx.x * 32;
-  if (c0 >= it.ncols || it.n == 0) return;
-  int nc = min(32, it.ncols - c0);
-  int n = it.n;
-  const double* A = it.a;
-  const int ld = it.ld;
-  double* X = it.x + (size_t)c0 * it.ldx;
-  const int ldx = it.ldx;
-  int lane = threadIdx.x & 31, grp = threadIdx.x >> 5, ngrp = blockDim.x >> 5;
-  // interchanges
-  if (grp == 0 && lane < nc)
-    for (int k = 0; k < n; ++k) {
-      int p = it.ipiv[k];
-      if (p != k) {
-        double t = X[k + (size_t)lane * ldx];
-        X[k + (size_t)lane * ldx] = X[p + (size_t)lane * ldx];
-        X[p + (size_t)lane * ldx] = t;
-      }
-    }
-  __syncthreads();
-  // forward: unit lower
-  for (int k = 0; k < n; ++k) {
-    double xk = lane < nc ? X[k + (size_t)lane * ldx] : 0.0;
-    for (int i = k + 1 + grp; i < n; i += ngrp)
-      if (lane < nc) X[i + (size_t)lane * ldx] -= A[i + (size_t)k * ld] * xk;
-    __syncthreads();
-  }
-  // backward: upper
-  for (int k = n - 1; k >= 0; --k) {
-    if (grp == 0 && lane < nc) X[k + (size_t)lane * ldx] /= A[k + (size_t)k * ld];
-    __syncthreads();
-    double xk = lane < nc ? X[k + (size_t)lane * ldx] : 0.0;
-    for (int i = grp; i < k; i += ngrp)
-      if (lane < nc) X[i + (size_t)lane * ldx] -= A[i + (size_t)k * ld] * xk;
-    __syncthreads();
-  }
-}
 
 // column maxima of |A| (n x n), one block per item
 static __global__ void k_colmax(const LuItem* items, double* out, int stride) {
@@ -710,7 +621,7 @@ static __global__ void __launch_bounds__(128) k_lu_laswp(const LuItem* items, in
 static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items, int k0, int maxh, int* err) {
   LuItem it = items[blockIdx.x];
   if (k0 >= it.n || it.n - k0 <= maxh) return;
-  // same algorithm as k_lu_panel, full-row interchanges
+  // the panel algorithm of k_lu_panel_sm in global memory, full-row interchanges
   __shared__ double shv[32];
   __shared__ int shi[32];
   int n = it.n;
