@@ -379,6 +379,7 @@ def main():
            "config": {"workload": f"log2d N={args.n}: uniform [-1,1]^2 (seed 1), A_ij=log|x_i-x_j|, A_ii=N, "
                                   "leaf 64, NNCA/RRQR tol 1e-10, nrhs 1 (metric) and 64",
                       "levels": stats0["levels"], "max_rank": stats0["max_rank_factor"],
+                      "gb_resident": stats0["bytes_resident"] / 1e9,
                       "l2": "inputs larger than L2 (factor storage >> 129 MB)",
                       "parallelism": "replicas" if ws > 1 else "single GPU",
                       "step": "build + factor + solve(nrhs=1) + solve(nrhs=64)"},
