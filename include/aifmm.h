@@ -84,9 +84,11 @@ typedef struct {
                       place of tol (the NNCA operators and aifmm_matvec keep tol);
                       a looser value gives the low-accuracy factorisation used as a
                       GMRES preconditioner (Sec. 4, Experiment 5). 0: tol */
-  int fma_gemm;    /* 0 (default): the Schur-update tile products run on the BF16
-                      tensor cores in FP64 precision (exact 7-bit integer digits,
-                      see aifmm_kernels.h); 1: on FP64 FMAs */
+  int fma_gemm;    /* 0 (default): the factorisation's tile products -- Schur update,
+                      compress fills and projections (7 digits), Z = Piv^-1 B and the
+                      pivot LU's trailing updates (8 digits, balanced) -- run on the
+                      BF16 tensor cores in FP64 precision (exact 7-bit integer digits,
+                      see aifmm_kernels.h); 1: all of them on FP64 FMAs */
   int tcgen05;     /* 1: the Schur-update tiles issue the same digit products on the
                       5th-generation tensor cores (tcgen05.mma, accumulators in tensor
                       memory; aifmm_dgemm_tc05) instead of warp MMAs; same accuracy,

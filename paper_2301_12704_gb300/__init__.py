@@ -131,7 +131,8 @@ def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, le
     ``symmetric=False`` selects the general elimination (rows and columns
     compressed separately, every Schur block computed); ``factor_tol`` > 0 is
     the compress threshold of the factorisation (default: ``tol``);
-    ``fma_gemm`` runs the Schur tiles on FP64 FMAs instead of the tensor cores;
+    ``fma_gemm`` runs the factorisation's tile products on FP64 FMAs instead of
+    the tensor cores;
     ``tcgen05`` issues them on tcgen05.mma instead of warp MMAs; ``fp32``
     makes the factorisation's tile products FP32 (a preconditioner for
     aifmm_gmres)."""
