@@ -144,10 +144,10 @@ template <int PM>
 __device__ inline void tile_gemm(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int mr,
                                  int nc, int K, double alpha) {
   if (PM == PM_OZ && nc > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
+    extern __shared__ __align__(16) unsigned char oz_dyn[];
     tile_gemm_64_oz<false>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
   } else if (PM == PM_OZ8 && nc > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
+    extern __shared__ __align__(16) unsigned char oz_dyn[];
     tile_gemm_64_oz<false, true, OZ_S8>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
   } else if (PM == PM_F32) {
     tile_gemm_64<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
@@ -509,7 +509,7 @@ template <int PM>
 __device__ inline void tile_gemm_tn(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int mr,
                                     int nc, int K, double alpha) {
   if (PM == PM_OZ && nc > THIN_NC) {
-    extern __shared__ unsigned char oz_dyn[];
+    extern __shared__ __align__(16) unsigned char oz_dyn[];
     tile_gemm_64_oz<true>(A, lda, B, ldb, C, ldc, min(64, mr), min(64, nc), K, alpha, oz_dyn);
   } else if (PM == PM_F32) {
     tile_gemm_64_tn<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);

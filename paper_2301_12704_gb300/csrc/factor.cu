@@ -1191,10 +1191,10 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   const double* A = R.type == 0 ? v.xx(R.box, sp) : v.lx(R.box, sp);
   int lda = R.type == 0 ? v.M : v.R;
   if (PM == PM_TC05) {
-    extern __shared__ unsigned char ozs[];
+    extern __shared__ __align__(16) unsigned char ozs[];
     tile_gemm_64_tc(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs, e.err);
   } else if (PM == PM_OZ) {
-    extern __shared__ unsigned char ozs[];
+    extern __shared__ __align__(16) unsigned char ozs[];
     tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
 
   } else if (PM == PM_F32) {

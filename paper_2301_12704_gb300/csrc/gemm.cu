@@ -13,7 +13,7 @@ namespace {
 template <bool KB, int S>
 __global__ void __launch_bounds__(256) k_gemm_oz(const double* A, int64_t lda, const double* B, int64_t ldb,
                                                  double* C, int64_t ldc, int m, int n, int k, double alpha) {
-  extern __shared__ unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   tile_gemm_64_oz<false, KB, S>(A + i0, (int)lda, B + (size_t)j0 * ldb, (int)ldb, C + i0 + (size_t)j0 * ldc, (int)ldc,
                   min(64, m - i0), min(64, n - j0), k, alpha, smem);
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) k_gemm_oz(const double* A, int64_t lda, c
 __global__ void __launch_bounds__(256) k_gemm_tc05(const double* A, int64_t lda, const double* B, int64_t ldb,
                                                    double* C, int64_t ldc, int m, int n, int k, double alpha,
                                                    int* err) {
-  extern __shared__ unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   tile_gemm_64_tc(A + i0, (int)lda, B + (size_t)j0 * ldb, (int)ldb, C + i0 + (size_t)j0 * ldc, (int)ldc,
                   min(64, m - i0), min(64, n - j0), k, alpha, smem, err);

@@ -22,9 +22,10 @@
 //    of K stay below 5 * 32 * 2^14 < 2^22 and are exact; the pairs with
 //    s + t = 5..8 (weight 2^-35 and below) share one FP32 accumulator whose
 //    truncation stays near 2^-54 of the tile's scale;
-//  * every 32 of K the exact weights are summed as one 64-bit integer, the
-//    rest added in FP64, and the result scaled by 2^(E_row + E_col) into the
-//    FP64 result registers.
+//  * every 32 of K the exact weights are summed into one 64-bit integer and
+//    the rest into FP32; once per K chunk (two such halves, one set of row
+//    and column exponents) the two are added in FP64 and the result scaled
+//    by 2^(E_row + E_col) into the FP64 result registers.
 // Pairs with s + t > 8 are dropped: a digit pair contributes up to 2^14 times
 // its weight, so s + t = 7, 8 still matter at the 2^-48 level while s + t >= 9
 // is below 2^-49 of the top digits' product: 39 digit-pair MMAs per 16-deep
@@ -61,7 +62,7 @@ __device__ inline int oz_bexp(double x) {
 // exact), a = sum_s d_s 2^(7 (S - 1 - s)); written as BF16 values
 // +-d_s 2^(-7 s), so that |x| = 2^(E - 1029) sum_s value_s for every S
 template <int S = OZ_S>
-__device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride) {
+__device__ inline void oz_digit_bits(double x, int E, uint16_t (&out)[S]) {
   long long bits = __double_as_longlong(x);
   int e = (int)((bits >> 52) & 0x7ff);
   unsigned long long a = 0;
@@ -77,9 +78,17 @@ __device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride
   for (int s = 0; s < S; ++s) {
     unsigned d = s == 0 ? (unsigned)(a >> (7 * (S - 1))) : (unsigned)((a >> (7 * (S - 1 - s))) & 0x7f);
     float v = (float)d * scale;
-    out[s * stride] = __float2bfloat16_rn(neg ? -v : v);
+    out[s] = __bfloat16_as_ushort(__float2bfloat16_rn(neg ? -v : v));
     scale *= 0.0078125f;                 // 2^-7
   }
+}
+
+template <int S = OZ_S>
+__device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride) {
+  uint16_t d[S];
+  oz_digit_bits<S>(x, E, d);
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[s * stride] = __ushort_as_bfloat16(d[s]);
 }
 
 __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
@@ -203,16 +212,8 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
       }
     }
     __syncthreads();
-    // ---- stage: digits into shared memory
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int i = TA ? 8 * w + q : lane + 32 * h;
-        int k = TA ? lane + 32 * h : 8 * w + q;
-        oz_digits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
-      }
-    }
+    // ---- stage: digits into shared memory (B first: its registers are free
+    // before the A digits are packed)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int j = 8 * w + q;
@@ -222,10 +223,49 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
         oz_digits<S>(bv[q][h], KB ? eb[j] + (ek[k] - 1023) : eb[j], Bs + j * OZ_LD + k, 64 * OZ_LD);
       }
     }
+    if (TA) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int i = 8 * w + q, k = lane + 32 * h;
+          oz_digits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
+        }
+      }
+    } else {
+      // a lane holds k = 8w..8w+7 of its row: one 16-byte store per digit
+      // (rows 144 bytes apart: eight lanes cover the 32 banks once)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        uint32_t pk[S][4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = 8 * w + q;
+          uint16_t d[S];
+          oz_digit_bits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], d);
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            if (q & 1) pk[s][q >> 1] |= (uint32_t)d[s] << 16;
+            else pk[s][q >> 1] = d[s];
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          *reinterpret_cast<uint4*>(As + s * 64 * OZ_LD + i * OZ_LD + 8 * w) =
+              make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+      }
+    }
     __syncthreads();
     // ---- MMAs, flushed every 32 of K: digit-pair weights s + t = 0..4 each
-    // in its own accumulator (exact), 5..8 together
+    // in its own accumulator (exact), 5..8 together.  The two halves of a
+    // chunk share the row and column scales, so the exact part is carried
+    // from the first to the second as a 64-bit integer (and the rest as
+    // FP32) and converted and scaled in FP64 once per chunk.
+    long long tot[2][2][4];
+    float r5[2][2][4];
     for (int kh = 0; kh < OZ_KC; kh += 32) {
+      const bool first = kh == 0;
       float acc[6][2][2][4];
 #pragma unroll
       for (int x = 0; x < 6; ++x)
@@ -269,26 +309,32 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
         }
       }
       // ---- recombine: the exact weights as one 64-bit integer in units of
-      // 2^-28, the rest in FP32, then the row and column scales in FP64
+      // 2^-28, the rest in FP32; after the second half the row and column
+      // scales in FP64
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
-            long long tot = 0;
+            long long t = first ? 0 : tot[a][b][q];
             float wgt = 1.0f;
 #pragma unroll
             for (int x = 0; x < 5; ++x) {
-              tot += (long long)__float2int_rn(acc[x][a][b][q] * wgt) * (1ll << (7 * (4 - x)));
+              t += (long long)__float2int_rn(acc[x][a][b][q] * wgt) * (1ll << (7 * (4 - x)));
               wgt *= 128.0f;
             }
-            double sum = fma((double)tot, 0x1p-28, (double)acc[5][a][b][q]);
-            // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
-            int be = ea[i] + eb[j] - 2058 + 1023;
-            double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
-            acc64[a][b][q] = fma(sum, sc, acc64[a][b][q]);
+            if (first) {
+              tot[a][b][q] = t;
+              r5[a][b][q] = acc[5][a][b][q];
+            } else {
+              int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
+              double sum = fma((double)t, 0x1p-28, (double)(acc[5][a][b][q] + r5[a][b][q]));
+              // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
+              int be = ea[i] + eb[j] - 2058 + 1023;
+              double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
+              acc64[a][b][q] = fma(sum, sc, acc64[a][b][q]);
+            }
           }
     }
     __syncthreads();
