@@ -175,6 +175,24 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
+// four warp sums at once, the result in every lane: a transposing butterfly
+// (the first two steps halve the values a lane keeps, so lane groups of 8
+// finish one sum each), 6 FP64 additions instead of 20, then a broadcast
+__device__ inline void warp_sum4(double (&v)[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  double k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+  k0 += __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[2], 16);
+  k1 += __shfl_xor_sync(0xffffffffu, h16 ? v[1] : v[3], 16);
+  double s = h8 ? k1 : k0;                         // sum number 2 h16 + h8
+  s += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) v[u] = __shfl_sync(0xffffffffu, s, 8 * u);
+}
+
 // argmax of |v| with the lowest index on ties; returns (value, index)
 struct ArgMax {
   double v;

@@ -508,10 +508,7 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) dt[u] += vi * col[u][i];
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(0xffffffffu, dt[u], o);
+      warp_sum4(dt);
       double xk[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = k + lane; i < m; i += 32) {
         double vi = vref[i];
@@ -576,10 +573,7 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) dt[u] += vi * qc[u][i];
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(0xffffffffu, dt[u], o);
+      warp_sum4(dt);
       for (int i = kk + lane; i < m; i += 32) {
         double vi = vk[i];
 #pragma unroll
