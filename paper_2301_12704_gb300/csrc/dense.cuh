@@ -214,12 +214,21 @@ static __global__ void __launch_bounds__(128) k_lus_swap(const SolveItem* items)
 
 constexpr int TB = 64;   // diagonal block of the blocked triangular solves
 
+// Divisions by a pivot or a diagonal entry of U are multiplications by its
+// reciprocal, taken once (an FP64 division is a multi-instruction sequence
+// on the narrow FP64 pipe, and in the triangular solves it sat on the
+// dependency chain); one more rounding than a division, as in LAPACK's
+// unblocked LU.  The LU panels reject pivots below the smallest normal
+// number as singular, so every reciprocal is finite.
+constexpr double LU_PIV_MIN = 2.2250738585072014e-308;
+
 // diagonal block k0..k0+TB of the unit-lower (lower=1) or upper (lower=0)
 // factor applied to every column; the block sits in shared memory, one
 // thread per column keeps its TB entries in registers.
 template <int LOWER>
 static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items, int k0) {
   __shared__ double T[TB][TB + 1];
+  __shared__ double Rd[TB];              // upper: reciprocals of the diagonal
   SolveItem it = items[blockIdx.y];
   int n = it.n;
   if (k0 >= n) return;
@@ -229,6 +238,10 @@ static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items,
     T[i][j] = (i < nb && j < nb) ? it.a[(k0 + i) + (size_t)(k0 + j) * it.ld] : 0.0;
   }
   __syncthreads();
+  if (!LOWER) {
+    if (threadIdx.x < TB) Rd[threadIdx.x] = threadIdx.x < nb ? 1.0 / T[threadIdx.x][threadIdx.x] : 0.0;
+    __syncthreads();
+  }
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= it.ncols) return;
   double* X = it.x + (size_t)c * it.ldx + k0;
@@ -243,7 +256,7 @@ static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items,
   } else {
 #pragma unroll
     for (int j = TB - 1; j >= 0; --j) {
-      if (j < nb) x[j] /= T[j][j];
+      if (j < nb) x[j] *= Rd[j];
 #pragma unroll
       for (int i = 0; i < j; ++i) x[i] -= T[i][j] * x[j];
     }
@@ -261,6 +274,7 @@ static __global__ void __launch_bounds__(128) k_lus_diag(const SolveItem* items,
 template <int LOWER>
 static __global__ void __launch_bounds__(128) k_lus_diag_w(const SolveItem* items, int k0) {
   __shared__ double T[TB][TB + 1];
+  __shared__ double Rd[TB];              // upper: reciprocals of the diagonal
   SolveItem it = items[blockIdx.y];
   int n = it.n;
   if (k0 >= n) return;
@@ -270,6 +284,10 @@ static __global__ void __launch_bounds__(128) k_lus_diag_w(const SolveItem* item
     T[i][j] = (i < nb && j < nb) ? it.a[(k0 + i) + (size_t)(k0 + j) * it.ld] : 0.0;
   }
   __syncthreads();
+  if (!LOWER) {
+    if (threadIdx.x < TB) Rd[threadIdx.x] = threadIdx.x < nb ? 1.0 / T[threadIdx.x][threadIdx.x] : 0.0;
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, c = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (c >= it.ncols) return;
   double* X = it.x + (size_t)c * it.ldx + k0;
@@ -283,9 +301,9 @@ static __global__ void __launch_bounds__(128) k_lus_diag_w(const SolveItem* item
   } else {
     for (int j = nb - 1; j >= 0; --j) {
       if (j < 32) {
-        if (lane == j) x0 /= T[j][j];
+        if (lane == j) x0 *= Rd[j];
       } else if (lane == j - 32) {
-        x1 /= T[j][j];
+        x1 *= Rd[j];
       }
       double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
       if (lane < j) x0 -= T[lane][j] * xj;
@@ -384,12 +402,14 @@ static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items
       double x[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[c] = lane < kb ? xs[k0 + lane + c * n] : 0.0;
+      // reciprocals of the block's diagonal, one per lane, before the chain
+      const double rdl = lane < kb ? 1.0 / A[(k0 + lane) + (size_t)(k0 + lane) * ld] : 0.0;
       for (int j = kb - 1; j >= 0; --j) {
-        const double d = A[(k0 + j) + (size_t)(k0 + j) * ld];
+        const double rd = __shfl_sync(0xffffffffu, rdl, j);
         const double u = lane < j ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const double xj = __shfl_sync(0xffffffffu, x[c], j) / d;
+          const double xj = __shfl_sync(0xffffffffu, x[c], j) * rd;
           if (lane == j) x[c] = xj;
           x[c] -= u * xj;
         }
@@ -567,7 +587,7 @@ static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items,
         }
       }
       double cm = it.colmax ? it.colmax[k0 + jj] : 0.0;
-      if (!(bv > 1e-14 * cm) || !(bv > 0.0)) {
+      if (!(bv > 1e-14 * cm) || !(bv >= LU_PIV_MIN)) {
         if (lane == 0) sing = 1;
       } else {
         if (lane == 0) it.ipiv[k0 + jj] = k0 + bi;
@@ -583,9 +603,9 @@ static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items,
       if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
       return;
     }
-    const double piv = Ps[jj + (size_t)jj * h];
+    const double rpiv = 1.0 / Ps[jj + (size_t)jj * h];
     for (int i = jj + 1 + threadIdx.x; i < h; i += blockDim.x) {
-      double l = Ps[i + (size_t)jj * h] / piv;
+      double l = Ps[i + (size_t)jj * h] * rpiv;
       Ps[i + (size_t)jj * h] = l;
       for (int cc = jj + 1; cc < nbw; ++cc) Ps[i + (size_t)cc * h] -= l * Ps[jj + (size_t)cc * h];
     }
@@ -641,7 +661,7 @@ static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items
     best = block_amax(best, shv, shi);
     int p = best.i;
     double cm = it.colmax ? it.colmax[j] : 0.0;
-    if (!(best.v > 1e-14 * cm) || !(best.v > 0.0)) {
+    if (!(best.v > 1e-14 * cm) || !(best.v >= LU_PIV_MIN)) {
       if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
       return;
     }
@@ -653,8 +673,8 @@ static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items
         A[p + (size_t)c * ld] = t;
       }
     __syncthreads();
-    double piv = A[j + (size_t)j * ld];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (size_t)j * ld] /= piv;
+    const double rpiv = 1.0 / A[j + (size_t)j * ld];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (size_t)j * ld] *= rpiv;
     __syncthreads();
     int w = kend - j - 1, hh = n - j - 1;
     for (int e = threadIdx.x; e < w * hh; e += blockDim.x) {
