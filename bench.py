@@ -142,6 +142,8 @@ def reference_arm(args, ws, rank):
         return
     vals = []
     info = None
+    for _ in range(args.warmup):                      # untimed, as in the GPU arm
+        cpu_baseline(4096)
     for _ in range(max(1, args.steps)):
         info = cpu_baseline(4096)
         vals.append(info["value"])
@@ -150,7 +152,7 @@ def reference_arm(args, ws, rank):
     info["sample"] = "4,096-point log2d problem per step (same kernel, tol, leaf, density); " + info["sample"].split("; ", 1)[1]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "warmup": args.warmup, "ms_per_step": 1e3 * 4096 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": "log2d N=65536 (oracle timed on a 4,096-point sample)",
                                         "kernel": "log|x-y|, A_ii=N", "tol": 1e-10, "leaf": 64},
         "cpu_baseline": info, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
