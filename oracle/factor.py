@@ -45,6 +45,13 @@ Readings where the paper is silent or ambiguous (also listed in the design doc):
   symmetrically for P2P_qb).  In exact arithmetic this is the same
   redirection as the paper's two-sided P2P formula, split over the two
   boxes' steps.
+  Grouping 'pair' is Algorithm 2 as printed: before box i is eliminated,
+  each pending vP2P pair (i, q) has P2P_iq and P2P_qi compressed on both of
+  their boxes into the M2Ls A_iq, A_qi (Sec. 3.2.1), and each vP2L pair
+  (r, i) has P2L_ri and M2P_ir compressed on i's sides into A_ri, A_ir
+  (Secs. 3.2.2, 3.2.3); pairs in ascending partner order, ranks equalised
+  (R4) per box after each pair.  Both groupings are pinned against the
+  uncompressed elimination and against each other.
 * R3 RRQR: Householder QR with column pivoting in which the existing basis
   columns U_b are taken first, in order (so U_b = U~_b L_b holds to rounding,
   as the paper's eq. P2P_2a requires), followed by pivoting on the largest
@@ -63,7 +70,11 @@ Readings where the paper is silent or ambiguous (also listed in the design doc):
 Parity: pinned by (i) compression off == dense solve of A~ to 1e-12;
 (ii) compression on with eps_A -> 0 == dense solve of A to 1e-12;
 (iii) error against the dense solution falls with eps_A; (iv) paper order
-and colour order agree to a small multiple of eps_A (tests/test_oracle_factor.py).
+and colour order agree to a small multiple of eps_A; (v) both groupings stay
+within eps_A of the uncompressed elimination (tests/test_oracle_factor.py);
+(vi) one compress-and-redirect step leaves the Schur complement onto the
+uneliminated particles unchanged at threshold 0 and changes it by
+O(eps_A |F|) at eps_A (tests/test_oracle_redirect.py).
 """
 from __future__ import annotations
 
@@ -264,6 +275,211 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float):
     return rn - r
 
 
+# ---- the paper's literal grouping: pair by pair (Algorithm 2, vP2P / vP2L) --
+
+def _set_row_basis(S: BlockSystem, T, l: int, b: int, Ut: np.ndarray) -> np.ndarray:
+    """U_b := Ut, whose orthonormal columns span the old U_b, so that
+    U_b = Ut L_b with L_b = Ut^T U_b.  The locals row of b is multiplied by
+    L_b: its M2Ls A_bc (the "other M2L" update of Sec. 3.2.1), its L2L
+    U^dag_b (the L2L update) and any fill-in it holds.  Returns L_b."""
+    _ensure_aux(S, l, b)
+    Lb, zb = ("L", l, b), ("z", l, b)
+    rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
+    m = sum(S.rsize[k] for k in rs)
+    U = S.dense(rs, [zb]) if S.csize[zb] else np.zeros((m, 0))
+    Lm = Ut.T @ U
+    rn = Ut.shape[1]
+    old_row = {ck: S.pop(Lb, ck) for ck in list(S.rows[Lb])}
+    for rk in rs:
+        S.pop(rk, zb)
+    assert not S.cols[zb], "z_b column holds blocks outside X_b and its locals row"
+    _resize(S, Lb, rn, True)
+    _resize(S, zb, rn, False)
+    for ck, M in old_row.items():
+        if ck != zb:
+            S.set(Lb, ck, Lm @ M)
+    S.set(Lb, zb, -np.eye(rn))
+    off = 0
+    for rk in rs:
+        n = S.rsize[rk]
+        S.set(rk, zb, Ut[off:off + n])
+        off += n
+    return Lm
+
+
+def _set_col_basis(S: BlockSystem, T, l: int, b: int, Vt: np.ndarray) -> np.ndarray:
+    """V_b := Vt (orthonormal, spanning the old V_b: V_b = Vt R_b with
+    R_b = Vt^T V_b).  The multipole column of b is multiplied by R_b^T: the
+    M2Ls A_db (other M2L update), the parent's M2M V^dag*_b (M2M update) and
+    any fill-in it holds.  Returns R_b."""
+    _ensure_aux(S, l, b)
+    Yb, yb = ("Y", l, b), ("y", l, b)
+    cs = [k for k in colset(T, l, b) if S.csize.get(k, 0)]
+    m = sum(S.csize[k] for k in cs)
+    V = S.dense([Yb], cs).T if S.rsize[Yb] else np.zeros((m, 0))
+    Rm = Vt.T @ V
+    rn = Vt.shape[1]
+    old_col = {rk: S.pop(rk, yb) for rk in list(S.cols[yb])}
+    for ck in cs:
+        S.pop(Yb, ck)
+    assert not S.rows[Yb], "Y_b row holds blocks outside x_b and y_b"
+    _resize(S, Yb, rn, True)
+    _resize(S, yb, rn, False)
+    for rk, M in old_col.items():
+        if rk != Yb:
+            S.set(rk, yb, M @ Rm.T)
+    S.set(Yb, yb, -np.eye(rn))
+    off = 0
+    for ck in cs:
+        n = S.csize[ck]
+        S.set(Yb, ck, Vt[off:off + n].T)
+        off += n
+    return Rm
+
+
+def _grow(Q0: np.ndarray, F: np.ndarray, eps: float) -> np.ndarray:
+    """RRQR of [Q0 | F] with Q0's columns taken first (reading R3): the
+    orthonormal basis of Q0 plus the directions of F kept above
+    eps * max_j ||F_:j||."""
+    r = Q0.shape[1]
+    Q, d = qrcp_forced(np.hstack([Q0, F]), r)
+    tau = eps * (np.linalg.norm(F, axis=0).max() if F.shape[1] else 0.0)
+    return Q[:, :rrqr_rank(d, r, tau)]
+
+
+def _row_basis(S, T, l, b):
+    rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
+    zb = ("z", l, b)
+    m = sum(S.rsize[k] for k in rs)
+    return rs, (S.dense(rs, [zb]) if S.csize.get(zb, 0) else np.zeros((m, 0)))
+
+
+def _col_basis(S, T, l, b):
+    cs = [k for k in colset(T, l, b) if S.csize.get(k, 0)]
+    Yb = ("Y", l, b)
+    m = sum(S.csize[k] for k in cs)
+    return cs, (S.dense([Yb], cs).T if S.rsize.get(Yb, 0) else np.zeros((m, 0)))
+
+
+def compress_p2p(S: BlockSystem, T, l: int, i: int, j: int, eps: float) -> None:
+    """Sec. 3.2.1 for the fill-in P2P_ij (x_j -> x_i, both boxes not yet
+    eliminated): [U_i | P2P_ij] = U~_i [L_i | L~_ij], [V_j | L~_ij^*] =
+    V~_j [R_j | R~_ij]; A_ij := L_i A_ij R_j^* + R~_ij^*, U_i := U~_i,
+    V_j := V~_j, with the other M2L, M2M and L2L updates."""
+    _ensure_aux(S, l, i)
+    _ensure_aux(S, l, j)
+    rs, U = _row_basis(S, T, l, i)
+    cs, V = _col_basis(S, T, l, j)
+    P = S.dense(rs, cs)
+    if not rs or not cs or not np.any(P):
+        return
+    Ut = _grow(U, P, eps)
+    Lt = Ut.T @ P
+    Vt = _grow(V, Lt.T, eps)
+    Rt = Vt.T @ Lt.T
+    for rk in rs:
+        for ck in cs:
+            S.pop(rk, ck)
+    _set_row_basis(S, T, l, i, Ut)
+    _set_col_basis(S, T, l, j, Vt)
+    S.add(("L", l, i), ("y", l, j), Rt.T)
+
+
+def compress_p2l(S: BlockSystem, T, l: int, r: int, s: int, eps: float) -> None:
+    """Sec. 3.2.2 for the fill-in P2L_rs (x_s -> locals of the eliminated
+    box r): [V_s | P2L_rs^*] = V~_s [R_s | R~_rs]; A_rs := A_rs R_s^* +
+    R~_rs^*, V_s := V~_s, with the other M2L and M2M updates."""
+    _ensure_aux(S, l, s)
+    cs, V = _col_basis(S, T, l, s)
+    Lr = ("L", l, r)
+    P = S.dense([Lr], cs) if S.rsize.get(Lr, 0) else np.zeros((0, V.shape[0]))
+    if not np.any(P):
+        return
+    Vt = _grow(V, P.T, eps)
+    Rt = Vt.T @ P.T
+    for ck in cs:
+        S.pop(Lr, ck)
+    _set_col_basis(S, T, l, s, Vt)
+    S.add(Lr, ("y", l, s), Rt.T)
+
+
+def compress_m2p(S: BlockSystem, T, l: int, s: int, r: int, eps: float) -> None:
+    """Sec. 3.2.3 for the fill-in M2P_sr (multipoles of the eliminated box
+    r -> x_s): [U_s | M2P_sr] = U~_s [L_s | L~_sr]; A_sr := L_s A_sr +
+    L~_sr, U_s := U~_s, with the other M2L and L2L updates."""
+    _ensure_aux(S, l, s)
+    rs, U = _row_basis(S, T, l, s)
+    yr = ("y", l, r)
+    P = S.dense(rs, [yr]) if S.csize.get(yr, 0) else np.zeros((U.shape[0], 0))
+    if not np.any(P):
+        return
+    Ut = _grow(U, P, eps)
+    Lt = Ut.T @ P
+    for rk in rs:
+        S.pop(rk, yr)
+    _set_row_basis(S, T, l, s, Ut)
+    S.add(("L", l, s), yr, Lt)
+
+
+def equalise_box(S: BlockSystem, T, l: int, b: int) -> None:
+    """Reading R4 after a pair's compression: the side with fewer basis
+    columns is extended by the other side's extra columns, orthogonalised
+    against its own."""
+    _ensure_aux(S, l, b)
+    rU, rV = S.csize[("z", l, b)], S.rsize[("Y", l, b)]
+    if rU == rV:
+        return
+    _, U = _row_basis(S, T, l, b)
+    _, V = _col_basis(S, T, l, b)
+    if rU < rV:
+        Q, _ = qrcp_forced(np.hstack([U, V[:, rU:rV]]), rV)
+        _set_row_basis(S, T, l, b, Q[:, :rV])
+    else:
+        Q, _ = qrcp_forced(np.hstack([V, U[:, rV:rU]]), rU)
+        _set_col_basis(S, T, l, b, Q[:, :rU])
+
+
+def _partner(T, l: int, key):
+    """The level-l box and the kind ('p2p': not yet eliminated, 'p2l':
+    eliminated) behind a well-separated row or column key."""
+    if key[0] in ("x", "X"):
+        return "p2p", key[1]
+    lev, q = key[1], key[2]
+    if lev == l + 1:
+        return "p2p", T.parent(q)
+    return "p2l", q
+
+
+def compress_pairs(S: BlockSystem, T, l: int, i: int, eps: float) -> int:
+    """Algorithm 2 as printed: before box i is eliminated, every pending pair
+    holding i is compressed and redirected -- first the vP2P pairs (i, q),
+    both P2P_iq and P2P_qi, then the vP2L pairs (r, i), P2L_ri and M2P_ir.
+    A pair is pending when its well-separated fill-in blocks exist (set
+    semantics, reading R7); pairs are taken in ascending partner order."""
+    _ensure_aux(S, l, i)
+    rs = [k for k in rowset(T, l, i) if S.rsize.get(k, 0)]
+    cs = [k for k in colset(T, l, i) if S.csize.get(k, 0)]
+    found = set()
+    for rk in rs:
+        for ck in S.rows[rk]:
+            if _is_ws_col(T, l, i, ck):
+                found.add(_partner(T, l, ck))
+    for ck in cs:
+        for rk in S.cols[ck]:
+            if _is_ws_row(T, l, i, rk):
+                found.add(_partner(T, l, rk))
+    for kind, q in sorted(found, key=lambda t: (t[0] != "p2p", t[1])):
+        if kind == "p2p":
+            compress_p2p(S, T, l, i, q, eps)
+            compress_p2p(S, T, l, q, i, eps)
+            equalise_box(S, T, l, q)
+        else:
+            compress_p2l(S, T, l, q, i, eps)
+            compress_m2p(S, T, l, i, q, eps)
+        equalise_box(S, T, l, i)
+    return len(found)
+
+
 class Step:
     __slots__ = ("PR", "PC", "lu", "rows", "ARP", "cols", "APC", "box")
 
@@ -310,11 +526,15 @@ def eliminate(S: BlockSystem, PR, PC, box=None) -> Step:
     return Step(PR, PC, lu, rows, ARP, cols, APC, box)
 
 
-def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = True):
+def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = True, grouping: str = "box"):
     """Algorithm 2 on the extended system of (tree, kernel, nn).
 
     order    -- 'paper' or 'colour' (reading R1)
     compress -- False keeps every fill-in as a block (exact sparse LU of A~)
+    grouping -- 'box': all of a box's pending fill-ins in one RRQR per side
+                (reading R2, the GPU's form); 'pair': pair by pair, each
+                P2P fill-in compressed on both of its boxes (Algorithm 2 as
+                printed, Sec. 3.2.1-3.2.3)
     """
     T = tree
     S = assemble(T, kernel, nn)
@@ -322,7 +542,9 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
     F.sizes_r, F.sizes_c = S.rsize, S.csize
     for l in range(T.L, 1, -1):
         for b in T.order(l, order):
-            if compress:
+            if compress and grouping == "pair":
+                F.ncompress += compress_pairs(S, T, l, b, eps)
+            elif compress:
                 if compress_box(S, T, l, b, eps):
                     F.ncompress += 1
             PR = rowset(T, l, b) + [("Y", l, b)]

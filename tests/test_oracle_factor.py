@@ -98,6 +98,39 @@ def test_paper_and_colour_order_agree():
     assert np.linalg.norm(xp - xc) / np.linalg.norm(xc) < 10 * eps
 
 
+def test_pair_grouping_tiny_tolerance_reproduces_dense_solution():
+    """Algorithm 2 as printed (pair by pair, each P2P fill-in compressed on
+    both of its boxes, Sec. 3.2.1-3.2.3) keeps the eps_A -> 0 invariant."""
+    T, K, nn, bt = _problem(n=1024, leaf=16, eps=1e-15)
+    fac = F.factor(T, K, nn, 1e-15, order="paper", grouping="pair")
+    x = F.solve(fac, bt)
+    xd = np.linalg.solve(K.dense(T.points), bt)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-12
+    assert fac.ncompress > 0
+
+
+def test_pair_and_box_grouping_agree():
+    """Reading R2 (one RRQR per box side over all its pending fill-ins)
+    against the printed pair-by-pair grouping: both stay within eps_A of the
+    uncompressed elimination (an exact sparse LU of the same NNCA system),
+    and so of each other.  A_ii = 5 so that the fill-ins are not negligible
+    against the diagonal."""
+    eps = 1e-6
+    w = W.log2d(1024, seed=7, leaf=16, tol=eps, nrhs=2, diag=5.0)
+    pts, b = W.points_and_rhs(w)
+    T = Tree(pts, w.leaf)
+    K = Kernel(w.kernel, w.diag)
+    nn = NNCA(T, K, eps)
+    bt = b[T.perm]
+    xn = F.solve(F.factor(T, K, nn, eps, order="paper", compress=False), bt)
+    xb = F.solve(F.factor(T, K, nn, eps, order="paper", grouping="box"), bt)
+    xp = F.solve(F.factor(T, K, nn, eps, order="paper", grouping="pair"), bt)
+    rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
+    assert rel(xb, xn) < eps and rel(xp, xn) < eps
+    assert rel(xp, xb) < eps
+    assert rel(xb, xn) > 1e-12            # the compression did act
+
+
 def test_multiple_rhs_columns_are_independent():
     T, K, nn, bt = _problem(n=512, leaf=16, eps=1e-10)
     fac = F.factor(T, K, nn, 1e-10, order="colour")

@@ -1,5 +1,7 @@
 """Pin of one compress-and-redirect step of the oracle (Sec. 3.2.1-3.2.3,
-Algorithm 2) against what it must preserve.
+Algorithm 2) against what it must preserve, for both groupings: all of a
+box's fill-ins at once (reading R2) and pair by pair (Algorithm 2 as
+printed).
 
 Redirecting a box's pending well-separated fill-ins changes the extended
 system's auxiliary unknowns (new bases U~_b, V~_b; the fill-ins moved into
@@ -78,25 +80,30 @@ def state():
     return dict(S=S, T=T, L=L, b=target, m=T.count(L, target), keep=(keep_r, keep_c), G0=G0, nF=nF)
 
 
-def _redirect(st, eps):
+def _redirect(st, eps, grouping):
     S1 = copy.deepcopy(st["S"])
-    F.compress_box(S1, st["T"], st["L"], st["b"], eps)
+    if grouping == "box":
+        F.compress_box(S1, st["T"], st["L"], st["b"], eps)
+    else:
+        F.compress_pairs(S1, st["T"], st["L"], st["b"], eps)
     dG = np.linalg.norm(_reduced(S1, *st["keep"]) - st["G0"])
     return dG, S1.csize[("z", st["L"], st["b"])]
 
 
-def test_exact_redirect_preserves_the_operator(state):
-    dG, r = _redirect(state, 0.0)
+@pytest.mark.parametrize("grouping", ["box", "pair"])
+def test_exact_redirect_preserves_the_operator(state, grouping):
+    dG, r = _redirect(state, 0.0, grouping)
     assert r <= state["m"]
     # a dropped, mis-signed or transposed redirect of the fill-ins changes G
     # by about |F|; rounding of G leaves ~1e-6 |F| here
     assert dG <= 1e-5 * state["nF"], (dG, state["nF"])
 
 
-def test_truncated_redirect_changes_the_operator_by_order_eps(state):
+@pytest.mark.parametrize("grouping", ["box", "pair"])
+def test_truncated_redirect_changes_the_operator_by_order_eps(state, grouping):
     eps = 1e-4
-    d0, r0 = _redirect(state, 0.0)
-    dG, r = _redirect(state, eps)
+    d0, r0 = _redirect(state, 0.0, grouping)
+    dG, r = _redirect(state, eps, grouping)
     assert r < r0                      # directions were discarded
     assert dG <= 10.0 * eps * state["nF"], (dG, eps * state["nF"])
     assert dG >= 10.0 * d0             # the truncation is visible above rounding
