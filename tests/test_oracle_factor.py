@@ -90,6 +90,26 @@ def test_error_falls_with_tolerance():
     assert errs[-1] < 1e-10
 
 
+def test_error_roughly_flat_in_n():
+    """At a fixed eps_A the error against the dense solution stays roughly
+    constant as N grows (Sec. 4.1, inference 1), here across a change of
+    depth (L = 3 to 4)."""
+    eps, errs, depths = 1e-6, [], []
+    for n in (512, 1024, 2048):
+        w = W.log2d(n, seed=11, leaf=16, tol=eps, nrhs=1)
+        pts, b = W.points_and_rhs(w)
+        T = Tree(pts, w.leaf)
+        K = Kernel(w.kernel, w.diag)
+        nn = NNCA(T, K, eps)
+        bt = b[T.perm]
+        x = F.solve(F.factor(T, K, nn, eps, order="colour"), bt)
+        xd = np.linalg.solve(K.dense(T.points), bt)
+        errs.append(np.linalg.norm(x - xd) / np.linalg.norm(xd))
+        depths.append(T.L)
+    assert depths[0] < depths[-1]
+    assert max(errs) < 10 * min(errs) and max(errs) < 100 * eps, errs
+
+
 def test_paper_and_colour_order_agree():
     eps = 1e-10
     T, K, nn, bt = _problem(n=700, leaf=16, eps=eps)
