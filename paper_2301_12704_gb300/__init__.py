@@ -102,6 +102,19 @@ def _check(status, handle=None):
         raise AifmmError(status, msg.decode() if msg else "")
 
 
+def _f64(t):
+    """A torch tensor as float64 (the ABI's only element type)."""
+    import torch
+    return t if t.dtype == torch.float64 else t.to(torch.float64)
+
+
+def _rows(a, n, what):
+    """The library reads n rows of every vector or matrix it is given: refuse
+    a buffer with another row count before its pointer crosses the ABI."""
+    if a.shape[0] != n:
+        raise ValueError(f"{what} has {a.shape[0]} rows, the problem has {n} points")
+
+
 def _ptr(a):
     """(pointer, keepalive) of a float64 numpy array or torch tensor."""
     if isinstance(a, np.ndarray):
@@ -138,6 +151,10 @@ def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, le
     aifmm_gmres)."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
+    else:
+        points = _f64(points).contiguous()
+    if points.ndim != 2:
+        raise ValueError("points must be N x dim")
     n, dim = points.shape
     k = Kernel(kernel, dim, float(diag), float(length))
     o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
@@ -156,7 +173,7 @@ def _col_major(a):
     """Column-major float64 copy/view of a vector or N x nrhs matrix."""
     if isinstance(a, np.ndarray):
         return np.asfortranarray(a[:, None] if a.ndim == 1 else a, dtype=np.float64)
-    t = a[:, None] if a.dim() == 1 else a
+    t = _f64(a[:, None] if a.dim() == 1 else a)
     return t.t().contiguous().t()
 
 
@@ -170,6 +187,7 @@ def _empty_cm(a):
 def aifmm_solve(h: Handle, rhs):
     """x = A^-1 rhs (C: aifmm_solve); rhs N or N x nrhs, original order."""
     b = _col_major(rhs)
+    _rows(b, h.n, "rhs")
     x = _empty_cm(b)
     pb, kb = _ptr(b)
     px, kx = _ptr(x)
@@ -181,10 +199,16 @@ def aifmm_solve_noalloc(h: Handle, rhs, x):
     """x = A^-1 rhs without any device allocation (C: aifmm_solve_noalloc).
     rhs and x must be column-major float64 CUDA tensors of shape N x nrhs;
     x is written in place and returned."""
+    import torch
     if rhs.dim() == 1:
         rhs, x = rhs[:, None], x[:, None]
     if not (rhs.is_cuda and x.is_cuda and rhs.stride(0) == 1 and x.stride(0) == 1):
         raise ValueError("aifmm_solve_noalloc needs column-major CUDA tensors")
+    if rhs.dtype != torch.float64 or x.dtype != torch.float64:
+        raise ValueError("aifmm_solve_noalloc needs float64 tensors")
+    _rows(rhs, h.n, "rhs")
+    if tuple(x.shape) != tuple(rhs.shape) or (rhs.shape[1] > 1 and x.stride(1) != rhs.stride(1)):
+        raise ValueError("x must have rhs's shape and leading dimension")
     _check(lib().aifmm_solve_noalloc(h.raw, C.c_void_p(rhs.data_ptr()), C.c_void_p(x.data_ptr()),
                                      rhs.shape[1], rhs.stride(1) if rhs.shape[1] > 1 else h.n), h.raw)
     return x
@@ -196,6 +220,7 @@ def aifmm_noalloc_scratch_bytes() -> int:
 
 def _product(fn, h, xv):
     xx = _col_major(xv)
+    _rows(xx, h.n, "x")
     y = _empty_cm(xx)
     px, kx = _ptr(xx)
     py, ky = _ptr(y)
@@ -222,8 +247,9 @@ def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: in
         bb = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
         x = np.empty_like(bb)
     else:
-        bb = b.reshape(-1).contiguous()
+        bb = _f64(b).reshape(-1).contiguous()
         x = torch_empty_like(bb)
+    _rows(bb, h.n, "b")
     pb, kb = _ptr(bb)
     px, kx = _ptr(x)
     it = C.c_int(0)
@@ -240,9 +266,11 @@ def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = Fa
     """C_ += alpha A B on the tensor cores in FP64 precision (C: aifmm_dgemm_tc,
     aifmm_dgemm_tc05 with ``tcgen05``, aifmm_dgemm_tc8 with ``digits8``).
     A, B, C_ CUDA float64 tensors, column-major (e.g. ``t.t().contiguous().t()``)."""
+    import torch
     m, k = A.shape
     k2, n = B.shape
     assert k2 == k and tuple(C_.shape) == (m, n)
+    assert A.dtype == B.dtype == C_.dtype == torch.float64, "float64 tensors"
     def ld(t):
         assert t.is_cuda and (t.stride(0) == 1 or t.shape[0] == 1), "column-major CUDA tensors"
         return max(1, t.shape[0], t.stride(1) if t.shape[1] > 1 else 1)
