@@ -168,6 +168,25 @@ def test_three_dimensional_small():
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 100 * eps
 
 
+def test_three_dimensional_three_levels_tiny_tolerance():
+    """3D 1/r with three levels (L = 3), so that the octree's non-leaf
+    levels and their 27-box stencils are eliminated too: eps_A -> 0 gives
+    the dense solution.  (At sizes the oracle affords, 3D leaf boxes hold a
+    few points and their bases are full rank: this pins the elimination and
+    the level transitions, not the truncation, which the 2D pins cover.)"""
+    eps = 1e-15
+    w = W.invr3d(600, seed=5, leaf=4, tol=eps, nrhs=1)
+    pts, b = W.points_and_rhs(w)
+    T = Tree(pts, w.leaf)
+    K = Kernel(w.kernel, w.diag)
+    nn = NNCA(T, K, eps)
+    assert T.d == 3 and T.L == 3
+    bt = b[T.perm]
+    x = F.solve(F.factor(T, K, nn, eps, order="colour"), bt)
+    xd = np.linalg.solve(K.dense(T.points), bt)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-12
+
+
 def test_qrcp_forced_columns():
     rng = np.random.default_rng(3)
     U = np.linalg.qr(rng.standard_normal((30, 6)))[0]
