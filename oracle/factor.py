@@ -32,7 +32,7 @@ blocks this creates.  Nothing is skipped: the coupled rows and columns are
 read from the incidence sets, so with compression switched off the routine
 is an exact sparse LU of A~ (pinned against a dense solve of A~).
 
-Readings where the paper is silent or ambiguous (also listed in the design doc):
+Readings where the paper is silent or ambiguous:
 * R1 order: 'paper' = Morton order within a level; 'colour' = distance-2
   colour classes (Morton order inside a class).  Boxes of one colour have
   disjoint neighbourhoods, so they commute.

@@ -67,7 +67,7 @@ def test_elimination_without_compression_is_exact_lu():
 
 @pytest.mark.parametrize("order", ["paper", "colour"])
 def test_tiny_tolerance_reproduces_dense_solution(order):
-    """eps_A -> 0: the AIFMM solution tends to A^-1 b (spec invariant)."""
+    """eps_A -> 0: the AIFMM solution tends to A^-1 b (the full-rank invariant)."""
     T, K, nn, bt = _problem(n=1024, leaf=16, eps=1e-15)
     assert T.L == 3
     fac = F.factor(T, K, nn, 1e-15, order=order)

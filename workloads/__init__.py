@@ -53,7 +53,7 @@ def points_and_rhs(w: Workload, nrhs: int | None = None):
 def log2d(n: int, seed: int, leaf: int = 64, tol: float = 1e-10, nrhs: int = 1,
           diag: float | None = None) -> Workload:
     """2D log kernel A_ij = log|x_i - x_j|, A_ii = N (the diagonal of the
-    spec 2D configurations), points uniform in [-1,1]^2."""
+    2D benchmark configurations), points uniform in [-1,1]^2."""
     return Workload(f"log2d_N{n}", n, 2, -1.0, 1.0, seed, LOG2D,
                     float(n) if diag is None else diag, leaf, tol, nrhs)
 
