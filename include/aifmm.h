@@ -131,7 +131,7 @@ typedef struct {
  *   n         number of points N >= 1.
  *   k         kernel description (dim must be 2 or 3).
  *   tol       eps_A >= 0, shared by NNCA and RRQR (Sec. 4, notation table).
- *   leaf_size n_max >= 1, target points per leaf box (Algorithm 2, first step).
+ *   leaf_size n_max >= 1, target points per leaf box (the depth rule of Sec. 2.1).
  *   opt       may be NULL (defaults).
  *   out       receives the new handle (NULL on failure).
  * Errors: INVALID, OOM, CUDA, CAPACITY. */
