@@ -553,8 +553,8 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
             if st is not None:
                 F.steps.append(st)
             F.ranks[(l, b)] = S.csize.get(("z", l, b), 0)
-    # top: the level-2 locals equations in the level-2 multipoles (Alg. 3,
-    # "solve for the multipoles at level 2 directly")
+    # top: the level-2 locals equations in the level-2 multipoles, solved for
+    # directly (Algorithm 3)
     PR = sorted(k for k in S.rows if S.rows[k] and k[0] == "L")
     PC = sorted(k for k in S.cols if S.cols[k] and k[0] == "y")
     leftover = [k for k in S.rows if S.rows[k] and k not in PR]

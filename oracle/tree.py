@@ -6,7 +6,7 @@ Paper passages followed:
 * Sec. 2.1: the domain Omega is the smallest hypercube holding every point;
   level 0 is Omega and each box at level l splits into 2^d children.
 * The depth L (Sec. 2.1 and Algorithm 2).  The paper states L through the
-  leaf occupancy ("fewer than n_max" in Algorithm 2, "no more than n_max" in
+  leaf occupancy (strictly below n_max in Algorithm 2, at most n_max in
   Sec. 2.1).  Reading used here: the average-occupancy rule
   L = max(2, smallest l with (2^d)^l * n_max >= N); ``depth_rule='max'``
   gives the literal maximum-occupancy rule.
