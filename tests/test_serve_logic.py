@@ -105,3 +105,14 @@ def test_solves_on_a_failed_factorisation_are_answered(fake, monkeypatch):
     assert all(r.status == "error" for r in reqs if r.kind == "factor")
     assert all(r.status == "evicted" for r in reqs if r.kind == "solve")
     assert m["solve"]["done"] == 0
+
+
+@pytest.mark.parametrize("n,d", [(100, 2), (4096, 2), (4097, 2), (65536, 2), (30000, 3), (262144, 3)])
+def test_occupancy_follows_the_tree_depth_rule(n, d):
+    """The memory model's points per leaf box use the same depth as the
+    tree (average-occupancy rule, Sec. 2.1): N / 2^(d L)."""
+    import numpy as np
+    from oracle.tree import Tree
+    pts = np.random.default_rng(n + d).uniform(-1.0, 1.0, (n, d))
+    L = Tree(pts, 64).L
+    assert S._occupancy(n, d, 64) == pytest.approx(n / float(1 << (d * L)))
