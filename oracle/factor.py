@@ -181,9 +181,11 @@ def _resize(S, key, new, is_row):
     sizes[key] = new
 
 
-def compress_box(S: BlockSystem, T, l: int, b: int, eps: float):
+def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool = False):
     """Compress and redirect every pending well-separated fill-in of box b
-    (reading R2): row side into U_b, column side into V_b."""
+    (reading R2): row side into U_b, column side into V_b.  ``symmetric``
+    (reading R13, for A = A^T with V = U): the RRQR of the row side gives
+    both new bases, V~_b = U~_b."""
     _ensure_aux(S, l, b)
     Yb, Lb, yb, zb = ("Y", l, b), ("L", l, b), ("y", l, b), ("z", l, b)
     rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
@@ -205,11 +207,11 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float):
         return 0
     # ---- RRQR on both sides (R3) and equal ranks (R4)
     QU, dU = qrcp_forced(np.hstack([U, Frow]), r)
-    QV, dV = qrcp_forced(np.hstack([V, Fcol]), r)
+    QV, dV = (QU, dU) if symmetric else qrcp_forced(np.hstack([V, Fcol]), r)
     tauU = eps * (np.linalg.norm(Frow, axis=0).max() if Frow.shape[1] else 0.0)
     tauV = eps * (np.linalg.norm(Fcol, axis=0).max() if Fcol.shape[1] else 0.0)
     rU = rrqr_rank(dU, r, tauU)
-    rV = rrqr_rank(dV, r, tauV)
+    rV = rU if symmetric else rrqr_rank(dV, r, tauV)
     rn = max(rU, rV)
     assert rn <= m
     if rn == 0:
@@ -526,7 +528,8 @@ def eliminate(S: BlockSystem, PR, PC, box=None) -> Step:
     return Step(PR, PC, lu, rows, ARP, cols, APC, box)
 
 
-def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = True, grouping: str = "box"):
+def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = True, grouping: str = "box",
+           symmetric: bool = False):
     """Algorithm 2 on the extended system of (tree, kernel, nn).
 
     order    -- 'paper' or 'colour' (reading R1)
@@ -535,6 +538,8 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
                 (reading R2, the GPU's form); 'pair': pair by pair, each
                 P2P fill-in compressed on both of its boxes (Algorithm 2 as
                 printed, Sec. 3.2.1-3.2.3)
+    symmetric -- per-box grouping with one RRQR per box for both bases
+                (reading R13; the kernel must be symmetric)
     """
     T = tree
     S = assemble(T, kernel, nn)
@@ -545,7 +550,7 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
             if compress and grouping == "pair":
                 F.ncompress += compress_pairs(S, T, l, b, eps)
             elif compress:
-                if compress_box(S, T, l, b, eps):
+                if compress_box(S, T, l, b, eps, symmetric=symmetric):
                     F.ncompress += 1
             PR = rowset(T, l, b) + [("Y", l, b)]
             PC = colset(T, l, b) + [("z", l, b)]

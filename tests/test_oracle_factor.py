@@ -151,6 +151,28 @@ def test_pair_and_box_grouping_agree():
     assert rel(xb, xn) > 1e-12            # the compression did act
 
 
+def test_symmetric_and_general_compression_agree():
+    """Reading R13 (the GPU's default): for a symmetric kernel with V = U one
+    RRQR per box gives both new bases.  Against the general two-sided form
+    (two RRQRs whose kept directions differ near the threshold in floating
+    point): both within eps_A of the uncompressed elimination and of each
+    other, with ranks no higher."""
+    eps = 1e-6
+    w = W.log2d(1024, seed=7, leaf=16, tol=eps, nrhs=2, diag=5.0)
+    pts, b = W.points_and_rhs(w)
+    T = Tree(pts, w.leaf)
+    K = Kernel(w.kernel, w.diag)
+    nn = NNCA(T, K, eps)
+    bt = b[T.perm]
+    xn = F.solve(F.factor(T, K, nn, eps, order="paper", compress=False), bt)
+    fg = F.factor(T, K, nn, eps, order="paper")
+    fs = F.factor(T, K, nn, eps, order="paper", symmetric=True)
+    xg, xs = F.solve(fg, bt), F.solve(fs, bt)
+    rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
+    assert rel(xs, xn) < eps and rel(xs, xg) < eps
+    assert max(fs.ranks.values()) <= max(fg.ranks.values())
+
+
 def test_multiple_rhs_columns_are_independent():
     T, K, nn, bt = _problem(n=512, leaf=16, eps=1e-10)
     fac = F.factor(T, K, nn, 1e-10, order="colour")
