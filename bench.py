@@ -31,7 +31,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "factor+solve points/s at rel-err<=1e-8 vs FP64 oracle"
 UNIT = "points/s"
-FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 nominal (profiling recipe table); DFMA probe measured 1.20
+# Digit-pair BF16 MMAs per FP64 multiply-add of the 7-digit tensor-core tile
+# (pairs of digits s + t <= 8 of seven 7-bit digits per operand).
+OZ_PAIRS = 39
+# Roofline denominators when MEASURED_PEAKS.json is absent: the profiling
+# recipe's fallback (one earlier GB300 measurement).
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measured_peaks():
+    """HBM copy bandwidth and cuBLAS BF16 rates measured on this machine's
+    GB300s (MEASURED_PEAKS.json, written by the test driver), else the
+    fallback; with the source named."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "of measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "of fallback (profiling recipe)"
 
 
 def parse():
@@ -115,7 +132,8 @@ class Clocks:
 
 def cpu_baseline(n_sample=16384):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    same kernel, tolerance, leaf size and point density, 16,384 points."""
+    same kernel, tolerance, leaf size and point density, n_sample points, in
+    this process (the reference arm's steps)."""
     import numpy as np
     import workloads as W
     from oracle import factor as OF
@@ -135,6 +153,46 @@ def cpu_baseline(n_sample=16384):
     return {"value": n_sample / dt, "unit": UNIT, "cores": int(threads), "kind": "oracle",
             "sample": f"{n_sample}-point log2d problem (same kernel, tol 1e-10, leaf 64, density); "
                       f"factor+solve {dt:.1f} s, paper order, numpy/scipy BLAS threads"}
+
+
+def oracle_runs(n=4096, seed=0):
+    """The oracle on the small configuration at full size (4,096 points, the
+    same kernel, diagonal, tolerance and leaf size as the timed problem), as
+    child processes with their BLAS thread counts fixed: one thread in
+    paper (Morton) order, and all host cores in colour order.  The oracle's
+    boxes run one after another; its block operations use the BLAS threads."""
+    ncpu = os.cpu_count() or 1
+    out = {}
+    for key, threads, order in (("single_thread", 1, "paper"), ("all_cores", ncpu, "colour")):
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[v] = str(threads)
+        env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+        r = subprocess.run([sys.executable, "-m", "oracle.baseline", "--n", str(n), "--seed", str(seed),
+                            "--order", order], env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
+        if r.returncode != 0:
+            out[key] = {"error": (r.stderr or r.stdout)[-300:]}
+            continue
+        out[key] = json.loads(r.stdout.strip().splitlines()[-1])
+    return out
+
+
+def cpu_baseline_full(n=4096, seed=0):
+    """The GPU arm's cpu_baseline: oracle_runs; the faster of the two runs is
+    the value (with small blocks, BLAS threads can cost more than they give)."""
+    runs = oracle_runs(n, seed)
+    ok = {k: v for k, v in runs.items() if "points_per_s" in v}
+    if not ok:
+        return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": runs}
+    best = max(ok.values(), key=lambda r: r["points_per_s"])
+    desc = "; ".join(f"{r['threads']} BLAS thread(s), {r['order']} order: {r['points_per_s']:.1f} points/s "
+                     f"(factor {r['s_factor']:.2f} s + solve {r['s_solve']:.3f} s)" for r in ok.values())
+    return {"value": best["points_per_s"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
+            "sample": f"the {n}-point configuration of the same workload at full size (log2d, uniform "
+                      f"[-1,1]^2, seed {seed}, A_ii = N, leaf 64, tol 1e-10), factor+solve; {desc}; the value is "
+                      f"the faster run; the 65,536-point problem does not fit the bounded time (the oracle's "
+                      f"cost grows faster than N: about 37 s at 16,384 points)",
+            "runs": runs}
 
 
 def reference_arm(args, ws, rank):
@@ -327,25 +385,33 @@ def main():
     for _ in range(args.warmup):
         h, _, _, _ = step(False)
         A.aifmm_destroy(h)
-    # accuracy of the timed configuration: true residual with the exact
-    # direct-sum product (outside the timed region)
+    # accuracy of the timed configuration: true residuals of both solves with
+    # the exact direct-sum product (outside the timed region)
     h, x1, x64, _ = step(False)
     r = A.aifmm_direct_matvec(h, x1) - b1_d
     resid = float(torch.linalg.norm(r) / torch.linalg.norm(b1_d))
+    r = A.aifmm_direct_matvec(h, x64) - b64_d
+    resid64 = float((torch.linalg.norm(r, dim=0) / torch.linalg.norm(b64_d, dim=0)).max())
     stats0 = A.aifmm_stats(h)
     A.aifmm_destroy(h)
     del x1, x64, r
+    # roofline peaks: the FP64 / FP32 FMA rates measured on this GPU now, the
+    # HBM and BF16 ones from the pool's measurement
+    fp64_peak = A.aifmm_fma_rate(False, stream.cuda_stream)
+    fp32_peak = A.aifmm_fma_rate(True, stream.cuda_stream)
+    peaks, peak_src = measured_peaks()
 
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    times, groups_ms, groups_fl, groups_n, launches = [], [0.0] * 4, [0.0] * 4, [0] * 4, 0
+    NG = 5
+    times, groups_ms, groups_fl, groups_n, launches = [], [0.0] * NG, [0.0] * NG, [0] * NG, 0
     with Clocks(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             h, _, _, t = step(True)
             s = A.aifmm_stats(h)
-            for g in range(4):
+            for g in range(NG):
                 groups_ms[g] += s["group_ms"][g]
                 groups_fl[g] += s["group_flops"][g]
                 groups_n[g] += s["group_launches"][g]
@@ -365,15 +431,43 @@ def main():
     fs_ms, tstep = max_over_ranks([fs_ms, tstep], dev, ws)
     value = replica_value(ws, args.n, args.steps, fs_ms)
 
-    # dominant kernel group of the factorisation -> roofline (FP64 ALU bound)
-    names = ["compress", "pivot_lu", "z_solve", "schur"]
-    g = max(range(4), key=lambda i: groups_ms[i])
-    achieved = groups_fl[g] / (groups_ms[g] / 1e3) / 1e12 if groups_ms[g] > 0 else 0.0
-    roof = {"bound": "alu", "kernel": f"factor group '{names[g]}'", "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": None, "peak_source": "FP64 nominal of the profiling recipe (not in MEASURED_PEAKS.json)",
-            "launches": groups_n[g], "avg_launch_ms": groups_ms[g] / max(1, groups_n[g]),
-            "share_of_factor": groups_ms[g] / max(1e-9, tf)}
+    # rooflines of single kernels, from their CUDA-event times inside the
+    # timed steps (profile mode records events around each launch on the
+    # library's stream) and their algorithmic work counted from the run's
+    # block sizes
+    names = ["compress_other", "pivot_lu", "z_solve", "schur", "qrcp"]
+    G_SCHUR, G_QRCP = 3, 4
+
+    def kernel_roof(g):
+        ms, fl, nl = groups_ms[g], groups_fl[g], groups_n[g]
+        fp64 = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        base = {"launches": nl, "avg_launch_ms": ms / max(1, nl), "share_of_factor": ms / max(1e-9, tf),
+                "flops_per_launch": fl / max(1, nl), "traffic": None}
+        if g == G_QRCP:
+            base.update({"kernel": "k_cmp_qrcp", "bound": "alu", "achieved": fp64, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": fp64 / fp64_peak if fp64_peak else None,
+                         "peak_source": "FP64 FMA rate measured on this GPU by aifmm_fma_rate"})
+        else:
+            # FP64-precision products issued as BF16 digit-pair MMAs: the
+            # tensor pipe's work is OZ_PAIRS MMA flops per FP64 flop
+            tc = OZ_PAIRS * fp64
+            base.update({"kernel": "k_schur", "bound": "tensor", "achieved": tc, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": tc / peaks["bf16_tflops"],
+                         "peak_source": "BF16 dense burst " + peak_src,
+                         "fp64_equivalent_tflops": fp64,
+                         "fp64_equivalent_frac_of_fp64_fma": fp64 / fp64_peak if fp64_peak else None})
+        return base
+
+    roofs = {names[g]: kernel_roof(g) for g in (G_QRCP, G_SCHUR) if groups_ms[g] > 0}
+    dom = max((G_QRCP, G_SCHUR), key=lambda g: groups_ms[g])
+    roof = roofs[names[dom]]
+    # the solve with one right-hand side: HBM-bound by its algorithmic bytes
+    bsolve = stats0["bytes_solve"]
+    gbs = bsolve / (ts1 / args.steps / 1e3) / 1e9 if ts1 > 0 else 0.0
+    roofs["solve_nrhs1"] = {"kernel": "solve sweeps (k_fwd_*, k_lus_*, k_bwd_*), nrhs=1", "bound": "hbm",
+                            "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": gbs / peaks["hbm_gbs"], "bytes": bsolve, "traffic": None,
+                            "peak_source": "HBM copy " + peak_src}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tstep / args.steps, "higher_is_better": True,
@@ -388,12 +482,19 @@ def main():
            "ms_build": sum(t[0] for t in times) / args.steps, "ms_factor": tf / args.steps,
            "ms_solve_nrhs1": ts1 / args.steps, "ms_solve_nrhs64": ts64 / args.steps,
            "solves_per_s_nrhs64": 64.0 / (ts64 / args.steps / 1e3),
-           "residual_direct_sum": resid, "flops_factor": stats0["flops_factor"],
+           "residual_direct_sum": resid, "residual_direct_sum_nrhs64_max": resid64,
+           "flops_factor": stats0["flops_factor"],
            "factor_fp64_tflops": stats0["flops_factor"] / (tf / args.steps / 1e3) / 1e12,
            "group_ms_per_factor": {n: groups_ms[i] / args.steps for i, n in enumerate(names)},
            "group_tflops": {n: (groups_fl[i] / (groups_ms[i] / 1e3) / 1e12 if groups_ms[i] > 0 else 0.0)
                             for i, n in enumerate(names)},
-           "roofline": roof, "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall}
+           "roofline": roof, "rooflines": roofs,
+           "peaks": {"fp64_fma_tflops": fp64_peak, "fp32_fma_tflops": fp32_peak, **peaks,
+                     "source": "FMA rates: aifmm_fma_rate on this GPU before the timed steps; HBM, BF16: "
+                               + peak_src},
+           "bytes_solve": bsolve, "bytes_resident": stats0["bytes_resident"],
+           "bytes_resident_over_bytes_solve": stats0["bytes_resident"] / max(1.0, bsolve),
+           "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall}
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers (copies inside)
@@ -422,7 +523,7 @@ def main():
     if args.mixed3d:
         out["mixed3d"] = mixed3d(A, dev, n=args.mixed3d)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"] = cpu_baseline_full()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:

@@ -17,7 +17,14 @@
  *   Pointers: a "buffer" argument may point to host or device memory; the
  *     library detects which (cudaPointerGetAttributes) and copies host data
  *     through pinned staging on the handle's stream.  Device buffers must be
- *     on the handle's device.
+ *     on the handle's device (INVALID otherwise).
+ *   Device: the handle belongs to the device current at aifmm_build; every
+ *     later call makes that device current for its duration and restores the
+ *     caller's current device on return.
+ *   Streams: work runs on the handle's stream (aifmm_options.stream, or a
+ *     non-blocking stream the library creates).  The library does not order
+ *     itself after other streams: device buffers must be ready when a call
+ *     starts.
  *   Layout: points are row-major N x dim (point-major); right-hand sides and
  *     solutions are column-major N x nrhs with leading dimension ld >= N, in
  *     the caller's original point order.
@@ -114,16 +121,22 @@ typedef struct {
   int max_m;                /* largest pivot x-size over all levels */
   int top_size;             /* size of the dense level-1 system */
   double flops_factor;      /* algorithmic FP64 flops of the last factor */
-  double bytes_solve;       /* algorithmic bytes streamed by one solve sweep pair, nrhs=1 */
+  double bytes_solve;       /* algorithmic bytes of one solve with nrhs = 1 (after factor):
+                               the factor entries both sweeps read once each -- the pivot
+                               LUs twice, the coupled blocks of every pivot's rows and
+                               columns once, the top LU twice; 0 before factor */
   double bytes_resident;    /* device bytes held by the handle */
   double ms_build, ms_factor, ms_solve, ms_matvec;
   int64_t kernel_launches;  /* kernels launched by the handle so far */
   /* profile mode: CUDA-event time, algorithmic FP64 flops and launches of the
      factorisation's kernel groups, summed over the last aifmm_factor:
-     [0] compress and redirect, [1] pivot LU, [2] Z = Piv^-1 B, [3] Schur update */
-  double group_ms[4];
-  double group_flops[4];
-  int64_t group_launches[4];
+     [0] compress and redirect except the pivoted QR, [1] pivot LU,
+     [2] Z = Piv^-1 B, [3] Schur update (the one kernel k_schur),
+     [4] the pivoted QR of the compression (the one kernel k_cmp_qrcp);
+     [5..7] zero */
+  double group_ms[8];
+  double group_flops[8];
+  int64_t group_launches[8];
 } aifmm_stats_t;
 
 /* Build the tree, interaction lists, NNCA operators and extended system.
@@ -154,7 +167,7 @@ aifmm_status aifmm_solve(aifmm_h h, const double* rhs, double* x, int nrhs, int6
  * must not call cudaMalloc once their factorisation is resident -- e.g. a
  * request loop serving solves from a thread that runs under a strict
  * allocation budget or alongside code that forbids allocation.  The paper
- * has no counterpart; this is a deployment variant of Algorithm 3.
+ * has no counterpart to this call.
  *   rhs, x    DEVICE pointers only (host staging would need an allocation),
  *             N x nrhs column-major, leading dimension ld; may alias.
  * Temporaries live in one static device array of
@@ -163,6 +176,7 @@ aifmm_status aifmm_solve(aifmm_h h, const double* rhs, double* x, int nrhs, int6
  * looks up that array's device address; make it before any stream capture.
  * The array is shared by all calls and keeps the last call's contents: calls
  * whose work overlaps on the GPU (other streams, other threads) race on it.
+ * The call runs with the handle's device current (as every call here does).
  * Errors: STATE (no factor), INVALID (host pointers, nrhs < 1, ld < N),
  * CAPACITY (the problem and nrhs need more than the static array), CUDA. */
 aifmm_status aifmm_solve_noalloc(aifmm_h h, const double* rhs, double* x, int nrhs, int64_t ld);
@@ -207,13 +221,20 @@ aifmm_status aifmm_stats(aifmm_h h, aifmm_stats_t* out);
  *     ranks after factorisation (which = 1) of the 2^(dim*l) boxes.
  *   aifmm_level_pivots: for level l, the incoming row pivots t^{b,i} of
  *     every box as tree positions, concatenated in box order (sum of NNCA
- *     ranks entries). */
+ *     ranks entries), each box's in the order the pivot search took them.
+ *   aifmm_level_far_pivots: the same for the far-field pivots s^{b,i}
+ *     (Sec. 2.3, eq. NCA; points of the interaction-list boxes). */
 aifmm_status aifmm_tree_perm(aifmm_h h, int64_t* perm, int64_t* level_start);
 aifmm_status aifmm_level_ranks(aifmm_h h, int level, int which, int* ranks);
 aifmm_status aifmm_level_pivots(aifmm_h h, int level, int64_t* pivots);
+aifmm_status aifmm_level_far_pivots(aifmm_h h, int level, int64_t* pivots);
 
 /* Depth L of the handle's tree (0 if h is NULL). */
 int aifmm_levels(aifmm_h h);
+
+/* CUDA device index the handle belongs to (the device current at
+ * aifmm_build); -1 if h is NULL. */
+int aifmm_device(aifmm_h h);
 
 /* Message of the last error on h (or of the last failed aifmm_build when h is
  * NULL).  Valid until the next call on the handle. */

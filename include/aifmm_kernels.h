@@ -48,6 +48,14 @@ int aifmm_dgemm_tc8(const double* A, int64_t lda, const double* B, int64_t ldb, 
 int aifmm_dgemm_tc05(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                      int k, double alpha, void* stream);
 
+/* Measured FMA throughput of the current device, for roofline peaks: every
+ * thread of 8 x (SM count) CTAs of 256 threads runs 8 independent FMA chains
+ * of 16,384 steps; *tflops receives 2 x FMAs / time in TFLOP/s, the best of
+ * five timed launches after one warm-up (CUDA events on `stream`, NULL: the
+ * legacy default stream).  fp32 = 0: FP64 FMAs (DFMA), else FP32 FMAs.
+ * Returns 0, 1 (tflops NULL), 2 (allocation failed) or 6 (CUDA error). */
+int aifmm_fma_rate(int fp32, void* stream, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

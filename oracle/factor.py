@@ -142,6 +142,7 @@ class Factorization:
         self.order, self.compress = order, compress
         self.steps = []
         self.ranks = {}          # (l, b) -> final rank r_b
+        self.rrqr = {}           # (l, b) -> RRQR record of the box's compression (grouping 'box')
         self.ncompress = 0
 
 
@@ -181,11 +182,13 @@ def _resize(S, key, new, is_row):
     sizes[key] = new
 
 
-def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool = False):
+def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool = False, log: dict | None = None):
     """Compress and redirect every pending well-separated fill-in of box b
     (reading R2): row side into U_b, column side into V_b.  ``symmetric``
     (reading R13, for A = A^T with V = U): the RRQR of the row side gives
-    both new bases, V~_b = U~_b."""
+    both new bases, V~_b = U~_b.  ``log`` (optional dict) receives, under
+    (l, b), the row side's RRQR record: old rank, |R_kk| sequence, threshold
+    and new rank (recording only)."""
     _ensure_aux(S, l, b)
     Yb, Lb, yb, zb = ("Y", l, b), ("L", l, b), ("y", l, b), ("z", l, b)
     rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
@@ -213,6 +216,8 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool 
     rU = rrqr_rank(dU, r, tauU)
     rV = rU if symmetric else rrqr_rank(dV, r, tauV)
     rn = max(rU, rV)
+    if log is not None:
+        log[(l, b)] = {"r_old": r, "rdiag": np.array(dU), "tau": tauU, "rank": rn}
     assert rn <= m
     if rn == 0:
         # every fill-in column is exactly zero: drop them
@@ -550,7 +555,7 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
             if compress and grouping == "pair":
                 F.ncompress += compress_pairs(S, T, l, b, eps)
             elif compress:
-                if compress_box(S, T, l, b, eps, symmetric=symmetric):
+                if compress_box(S, T, l, b, eps, symmetric=symmetric, log=F.rrqr):
                     F.ncompress += 1
             PR = rowset(T, l, b) + [("Y", l, b)]
             PC = colset(T, l, b) + [("z", l, b)]

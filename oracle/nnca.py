@@ -41,8 +41,15 @@ import numpy as np
 import scipy.linalg as sla
 
 
-def aca(evalrow, evalcol, nr: int, nc: int, eps: float):
-    """ACA with partial pivoting.  Returns (pivot_rows, pivot_cols)."""
+def aca(evalrow, evalcol, nr: int, nc: int, eps: float, trace: list | None = None):
+    """ACA with partial pivoting.  Returns (pivot_rows, pivot_cols).
+
+    ``trace`` (a list, optional) receives one record per step with the
+    quantities each decision was taken on: the masked |residual row| from
+    which the column pivot was picked and the magnitude of the unreduced row
+    (the scale of its rounding), the two sides of the stopping test, and the
+    masked |residual column| from which the next row was picked with the
+    magnitude of the unreduced column.  Recording changes no arithmetic."""
     us, vs, prow, pcol = [], [], [], []
     if nr == 0 or nc == 0:
         return prow, pcol
@@ -67,6 +74,12 @@ def aca(evalrow, evalcol, nr: int, nc: int, eps: float):
             continue
         v = row / row[j]
         u = np.array(evalcol(j), dtype=np.float64)
+        rec = None
+        if trace is not None:
+            rec = {"row": i, "col": j, "row_abs": a.copy(),
+                   "row_scale": float(np.abs(np.array(evalrow(i), dtype=np.float64)).max()),
+                   "col_scale": float(np.abs(u).max())}
+            trace.append(rec)
         for uu, vv in zip(us, vs):
             u -= vv[j] * uu
         cross = 0.0
@@ -74,7 +87,11 @@ def aca(evalrow, evalcol, nr: int, nc: int, eps: float):
             cross += (uu @ u) * (vv @ v)
         nu, nv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
         frob2 += 2.0 * cross + (nu * nv) ** 2
+        if rec is not None:
+            rec["stop_lhs"], rec["stop_rhs"] = nu * nv, eps * np.sqrt(max(frob2, 0.0))
         if nu * nv <= eps * np.sqrt(max(frob2, 0.0)):
+            if rec is not None:
+                rec["stopped"] = True
             break                      # the small term is not kept
         us.append(u)
         vs.append(v)
@@ -84,6 +101,8 @@ def aca(evalrow, evalcol, nr: int, nc: int, eps: float):
         a = np.abs(u)
         a[used_r] = -1.0
         i = int(np.argmax(a))
+        if rec is not None:
+            rec["col_abs"] = a.copy()
         if a[i] < 0.0:
             break
     return prow, pcol
@@ -135,6 +154,25 @@ class NNCA:
                 self.far[l][b] = spiv
                 self.U[l][b] = U
                 self.rank[l][b] = r
+
+    def box_sets(self, l, b):
+        """(rows, far-field columns) of box b at level l, as tree positions:
+        the sets its pivots were searched in."""
+        T = self.tree
+        cols = [np.arange(*T.range(l, D), dtype=np.int64) for D in T.interaction_list(l, b)]
+        cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+        return self.rows[l][b], cols
+
+    def trace_box(self, l, b):
+        """Re-run the pivot search of box b at level l and return its trace
+        (see ``aca``); the operators are not touched."""
+        rows, cols = self.box_sets(l, b)
+        pts, kernel = self.tree.points, self.kernel
+        tr = []
+        aca(lambda i: kernel.block(pts, rows[i:i + 1], cols)[0],
+            lambda j: kernel.block(pts, rows, cols[j:j + 1])[:, 0],
+            len(rows), len(cols), self.eps, trace=tr)
+        return rows, cols, tr
 
     def V(self, l, b):
         """P2M side; equals U for the symmetric kernels in scope."""

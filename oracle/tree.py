@@ -72,7 +72,7 @@ def demorton(key: np.ndarray, d: int, bits: int) -> np.ndarray:
 class Tree:
     """The tree T^L over a point set (sources = targets, Sec. 4)."""
 
-    def __init__(self, points: np.ndarray, leaf: int, depth_rule: str = "average"):
+    def __init__(self, points: np.ndarray, leaf: int, depth_rule: str = "average", depth: int | None = None):
         pts = np.asarray(points, dtype=np.float64)
         self.N, self.d = pts.shape
         self.lo = pts.min(axis=0)
@@ -87,7 +87,9 @@ class Tree:
             key = morton(c, L)
             return np.bincount(key, minlength=1 << (self.d * L))
 
-        self.L = depth_for(self.N, self.d, leaf, depth_rule, cells)
+        # depth: the rule of Sec. 2.1 (reading R0), or a depth fixed by the
+        # caller (to reach pivot blocks of a given size in tests)
+        self.L = int(depth) if depth else depth_for(self.N, self.d, leaf, depth_rule, cells)
         L = self.L
         n = 1 << L
         c = np.floor(((pts - self.lo) * n) / self.side).astype(np.int64)

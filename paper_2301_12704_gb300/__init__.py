@@ -48,8 +48,8 @@ class Stats(C.Structure):
                 ("max_rank_factor", C.c_int), ("max_m", C.c_int), ("top_size", C.c_int),
                 ("flops_factor", C.c_double), ("bytes_solve", C.c_double), ("bytes_resident", C.c_double),
                 ("ms_build", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
-                ("ms_matvec", C.c_double), ("kernel_launches", C.c_int64), ("group_ms", C.c_double * 4),
-                ("group_flops", C.c_double * 4), ("group_launches", C.c_int64 * 4)]
+                ("ms_matvec", C.c_double), ("kernel_launches", C.c_int64), ("group_ms", C.c_double * 8),
+                ("group_flops", C.c_double * 8), ("group_launches", C.c_int64 * 8)]
 
 
 _lib = None
@@ -79,10 +79,14 @@ def lib():
         L.aifmm_dgemm_tc05.restype = C.c_int
         L.aifmm_dgemm_tc8.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
         L.aifmm_dgemm_tc8.restype = C.c_int
+        L.aifmm_fma_rate.argtypes = [cint, vp, C.POINTER(dbl)]
+        L.aifmm_fma_rate.restype = C.c_int
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
         L.aifmm_level_ranks.argtypes = [vp, cint, cint, vp]
         L.aifmm_level_pivots.argtypes = [vp, cint, vp]
+        L.aifmm_level_far_pivots.argtypes = [vp, cint, vp]
         L.aifmm_levels.argtypes = [vp]
+        L.aifmm_device.argtypes = [vp]
         L.aifmm_last_error.argtypes = [vp]
         L.aifmm_last_error.restype = C.c_char_p
         L.aifmm_destroy.argtypes = [vp]
@@ -90,7 +94,7 @@ def lib():
         for name in ("aifmm_build", "aifmm_factor", "aifmm_solve", "aifmm_solve_noalloc", "aifmm_matvec",
                      "aifmm_direct_matvec", "aifmm_gmres",
                      "aifmm_stats", "aifmm_tree_perm", "aifmm_level_ranks", "aifmm_level_pivots",
-                     "aifmm_levels"):
+                     "aifmm_level_far_pivots", "aifmm_levels", "aifmm_device"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -115,6 +119,24 @@ def _rows(a, n, what):
         raise ValueError(f"{what} has {a.shape[0]} rows, the problem has {n} points")
 
 
+def _ready(h, *arrays):
+    """The library runs on the handle's own CUDA stream and does not wait for
+    other streams.  Before a torch CUDA tensor's pointer crosses the ABI,
+    wait for torch's pending work on its device (the current stream, where
+    the tensor was filled or copied), and refuse a tensor on another GPU than
+    the handle's."""
+    synced = set()
+    for a in arrays:
+        if a is None or isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False):
+            continue
+        if h is not None and h.device is not None and a.device.index != h.device:
+            raise ValueError(f"tensor on cuda:{a.device.index}, the handle belongs to cuda:{h.device}")
+        if a.device.index not in synced:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
+            synced.add(a.device.index)
+
+
 def _ptr(a):
     """(pointer, keepalive) of a float64 numpy array or torch tensor."""
     if isinstance(a, np.ndarray):
@@ -123,10 +145,10 @@ def _ptr(a):
 
 
 class Handle:
-    """Owns one aifmm_h."""
+    """Owns one aifmm_h (``device``: the CUDA device index it belongs to)."""
 
-    def __init__(self, raw, n, dim):
-        self.raw, self.n, self.dim = raw, n, dim
+    def __init__(self, raw, n, dim, device=None):
+        self.raw, self.n, self.dim, self.device = raw, n, dim, device
 
     def __del__(self):
         try:
@@ -160,9 +182,10 @@ def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, le
     o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
                 float(factor_tol), int(bool(fma_gemm)), int(bool(tcgen05)), int(bool(fp32)))
     out = C.c_void_p()
+    _ready(None, points)
     p, keep = _ptr(points)
     _check(lib().aifmm_build(C.c_void_p(p), n, C.byref(k), float(tol), int(leaf_size), C.byref(o), C.byref(out)))
-    return Handle(out.value, n, dim)
+    return Handle(out.value, n, dim, lib().aifmm_device(out.value))
 
 
 def aifmm_factor(h: Handle) -> None:
@@ -189,6 +212,7 @@ def aifmm_solve(h: Handle, rhs):
     b = _col_major(rhs)
     _rows(b, h.n, "rhs")
     x = _empty_cm(b)
+    _ready(h, b, x)
     pb, kb = _ptr(b)
     px, kx = _ptr(x)
     _check(lib().aifmm_solve(h.raw, C.c_void_p(pb), C.c_void_p(px), b.shape[1], h.n), h.raw)
@@ -209,6 +233,7 @@ def aifmm_solve_noalloc(h: Handle, rhs, x):
     _rows(rhs, h.n, "rhs")
     if tuple(x.shape) != tuple(rhs.shape) or (rhs.shape[1] > 1 and x.stride(1) != rhs.stride(1)):
         raise ValueError("x must have rhs's shape and leading dimension")
+    _ready(h, rhs, x)
     _check(lib().aifmm_solve_noalloc(h.raw, C.c_void_p(rhs.data_ptr()), C.c_void_p(x.data_ptr()),
                                      rhs.shape[1], rhs.stride(1) if rhs.shape[1] > 1 else h.n), h.raw)
     return x
@@ -222,6 +247,7 @@ def _product(fn, h, xv):
     xx = _col_major(xv)
     _rows(xx, h.n, "x")
     y = _empty_cm(xx)
+    _ready(h, xx, y)
     px, kx = _ptr(xx)
     py, ky = _ptr(y)
     _check(fn(h.raw, C.c_void_p(px), C.c_void_p(py), xx.shape[1], h.n), h.raw)
@@ -250,6 +276,7 @@ def aifmm_gmres(h: Handle, b, rtol: float = 1e-10, maxit: int = 200, restart: in
         bb = _f64(b).reshape(-1).contiguous()
         x = torch_empty_like(bb)
     _rows(bb, h.n, "b")
+    _ready(h, bb, x)
     pb, kb = _ptr(bb)
     px, kx = _ptr(x)
     it = C.c_int(0)
@@ -281,6 +308,16 @@ def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = Fa
                               C.c_void_p(stream) if stream else None)
     if st != 0:
         raise AifmmError(st, "aifmm_dgemm_tc failed")
+
+
+def aifmm_fma_rate(fp32: bool = False, stream=None) -> float:
+    """Measured FMA rate of the current device in TFLOP/s (C: aifmm_fma_rate):
+    FP64 by default, FP32 with ``fp32``."""
+    r = C.c_double(0.0)
+    st = lib().aifmm_fma_rate(int(bool(fp32)), C.c_void_p(stream) if stream else None, C.byref(r))
+    if st != 0:
+        raise AifmmError(st, "aifmm_fma_rate failed")
+    return r.value
 
 
 def torch_empty_like(t):
@@ -320,6 +357,13 @@ def aifmm_level_pivots(h: Handle, level: int):
     r = aifmm_level_ranks(h, level, 0)
     p = np.empty(int(r.sum()), dtype=np.int64)
     _check(lib().aifmm_level_pivots(h.raw, level, C.c_void_p(p.ctypes.data)), h.raw)
+    return p
+
+
+def aifmm_level_far_pivots(h: Handle, level: int):
+    r = aifmm_level_ranks(h, level, 0)
+    p = np.empty(int(r.sum()), dtype=np.int64)
+    _check(lib().aifmm_level_far_pivots(h.raw, level, C.c_void_p(p.ctypes.data)), h.raw)
     return p
 
 

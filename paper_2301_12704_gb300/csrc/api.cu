@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstdint>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 
@@ -143,14 +144,70 @@ static aifmm_status to_status(int e) {
   }
 }
 
-static bool is_device_ptr(const void* p) {
+// Where a buffer lives: host memory (pageable or pinned), device memory of
+// the handle's GPU (or managed memory), or device memory of another GPU,
+// which no call accepts.
+enum PtrKind { P_HOST = 0, P_DEVICE = 1, P_OTHER_DEVICE = 2 };
+
+static int ptr_kind(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return P_HOST;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev ? P_DEVICE : P_OTHER_DEVICE;
+  if (a.type == cudaMemoryTypeManaged) return P_DEVICE;
+  return P_HOST;
 }
+
+static bool is_device_ptr(const void* p, int dev) { return ptr_kind(p, dev) == P_DEVICE; }
+
+// true if any of the buffers is device memory of another GPU (message set)
+static bool foreign(Handle& h, std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (p && ptr_kind(p, h.device) == P_OTHER_DEVICE) {
+      h.err = "a buffer is device memory of another GPU than the handle's (device " + std::to_string(h.device) + ")";
+      return true;
+    }
+  return false;
+}
+
+// Every call on a handle runs with the handle's device current and restores
+// the caller's current device on return, so a call made from a thread whose
+// current device is another GPU still launches, allocates and looks up
+// device symbols on the handle's GPU.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+      ok = false;
+      return;
+    }
+    if (prev != dev) {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+      }
+    } else {
+      prev = -1;   // nothing to restore
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+#define AIFMM_ON_DEVICE(h)                                              \
+  DeviceGuard _dg((h).device);                                          \
+  if (!_dg.ok) {                                                        \
+    (h).err = "cannot make device " + std::to_string((h).device) + " current"; \
+    return AIFMM_ERR_CUDA;                                              \
+  }
 
 struct Timer {
   cudaEvent_t a, b;
@@ -228,7 +285,12 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.derr = hnew<int>(h, 1);
   if (!h.derr) e = HOOM;
   const double* pdev = points;
-  if (!e && !is_device_ptr(points)) {
+  const int pk = ptr_kind(points, h.device);
+  if (!e && pk == P_OTHER_DEVICE) {
+    h.err = "points are device memory of another GPU than the current one";
+    e = HINVALID;
+  }
+  if (!e && pk == P_HOST) {
     double* tmp = hnew<double>(h, (size_t)n * h.d, false);
     if (!tmp) e = HOOM;
     else if (cudaMemcpyAsync(tmp, points, sizeof(double) * n * h.d, cudaMemcpyHostToDevice, h.stream) != cudaSuccess)
@@ -267,6 +329,7 @@ aifmm_status aifmm_factor(aifmm_h c) {
     h.err = "handle already factored";
     return AIFMM_ERR_STATE;
   }
+  AIFMM_ON_DEVICE(h);
   Timer tm(h.stream);
   int e = run_factor(h);
   if (!e) {
@@ -284,7 +347,7 @@ aifmm_status aifmm_factor(aifmm_h c) {
 
 // copy a column-major N x nrhs (ld) operand into the device buffer dst (ld)
 static int stage_in(Handle& h, const double* src, double* dst, int nrhs, int64_t ld) {
-  cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyKind kind = is_device_ptr(src, h.device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (src == dst) return HOK;
   AIFMM_CUDA_TRY(h, cudaMemcpy2DAsync(dst, ld * sizeof(double), src, ld * sizeof(double), h.N * sizeof(double),
                                       nrhs, kind, h.stream));
@@ -302,8 +365,10 @@ aifmm_status aifmm_solve(aifmm_h c, const double* rhs, double* x, int nrhs, int6
     h.err = "invalid argument";
     return AIFMM_ERR_INVALID;
   }
+  if (foreign(h, {rhs, x})) return AIFMM_ERR_INVALID;
+  AIFMM_ON_DEVICE(h);
   Timer tm(h.stream);
-  bool xdev = is_device_ptr(x);
+  bool xdev = is_device_ptr(x, h.device);
   double* work = xdev ? x : (double*)hscratch(h, 90, sizeof(double) * ld * nrhs);
   if (!work) return AIFMM_ERR_OOM;
   int e = stage_in(h, rhs, work, nrhs, ld);
@@ -339,10 +404,12 @@ aifmm_status aifmm_solve_noalloc(aifmm_h c, const double* rhs, double* x, int nr
     h.err = "invalid argument";
     return AIFMM_ERR_INVALID;
   }
-  if (!is_device_ptr(rhs) || !is_device_ptr(x)) {
-    h.err = "aifmm_solve_noalloc: rhs and x must be device pointers (host staging would allocate)";
+  if (!is_device_ptr(rhs, h.device) || !is_device_ptr(x, h.device)) {
+    h.err = "aifmm_solve_noalloc: rhs and x must be device pointers on the handle's GPU (host staging would "
+            "allocate)";
     return AIFMM_ERR_INVALID;
   }
+  AIFMM_ON_DEVICE(h);
   int e = HOK;
   if (rhs != x && cudaMemcpy2DAsync(x, ld * sizeof(double), rhs, ld * sizeof(double), h.N * sizeof(double), nrhs,
                                     cudaMemcpyDeviceToDevice, h.stream) != cudaSuccess) {
@@ -377,8 +444,10 @@ static aifmm_status product(aifmm_h c, const double* x, double* y, int nrhs, int
     h.err = "invalid argument";
     return AIFMM_ERR_INVALID;
   }
+  if (foreign(h, {x, y})) return AIFMM_ERR_INVALID;
+  AIFMM_ON_DEVICE(h);
   Timer tm(h.stream);
-  bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+  bool xdev = is_device_ptr(x, h.device), ydev = is_device_ptr(y, h.device);
   const double* xin = x;
   int e = HOK;
   if (!xdev) {
@@ -422,8 +491,10 @@ aifmm_status aifmm_gmres(aifmm_h c, const double* b, double* x, double rtol, int
     h.err = "invalid argument (rtol >= 0, maxit >= 1, 1 <= restart <= 512)";
     return AIFMM_ERR_INVALID;
   }
+  if (foreign(h, {b, x})) return AIFMM_ERR_INVALID;
+  AIFMM_ON_DEVICE(h);
   Timer tm(h.stream);
-  bool xdev = is_device_ptr(x);
+  bool xdev = is_device_ptr(x, h.device);
   double* bin = (double*)hscratch(h, 93, sizeof(double) * h.N);
   double* xout = xdev ? x : (double*)hscratch(h, 94, sizeof(double) * h.N);
   if (!bin || !xout) return AIFMM_ERR_OOM;
@@ -457,14 +528,40 @@ aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {
   o->max_m = h.max_m;
   o->top_size = h.ntop;
   o->flops_factor = h.flops_factor;
+  // algorithmic bytes of one solve with one right-hand side (Algorithm 3
+  // and the right-hand-side Schur operations): every stored factor entry the
+  // two sweeps must read, once each -- the pivot block's LU in both sweeps
+  // (n^2 entries per sweep), the blocks of the coupled rows in the pivot
+  // columns in the forward sweep (K_pb or P2L_pb: rows(p) x m_b) and of the
+  // pivot rows in the coupled columns in the backward sweep (K_bq or M2P_bq:
+  // m_b x cols(q)), rows/cols(p) = r_p if p was eliminated before b, else
+  // m_p -- and the top system's LU twice; vectors are not counted.
   double bytes = 0;
-  for (auto& F : h.fac) {
-    if (!F.nb) continue;
-    for (int b = 0; b < F.nb; ++b) {
-      double m = F.h_m[b], r = F.h_r[b], n = m + r;
-      // pivot LU + the coupled panels, read once per sweep (upper bound: 3^d blocks)
-      bytes += 8.0 * (n * n + 2.0 * std::pow(3.0, h.d) * m * m);
+  if (h.factored) {
+    for (auto& F : h.fac) {
+      if (!F.nb) continue;
+      for (int b = 0; b < F.nb; ++b) {
+        const double m = F.h_m[b], n = m + F.h_r[b];
+        if (m == 0) continue;
+        int bc[3], q[3];
+        morton_coords(b, h.d, F.l, bc);
+        const int cb = colour_of(bc, h.d);
+        double coupled = 0.0;
+        for (int o = 0; o < ipow(3, h.d); ++o) {
+          int oo = o;
+          for (int k = 0; k < 3; ++k) q[k] = bc[k];
+          for (int k = 0; k < h.d; ++k) {
+            q[k] = bc[k] + (oo % 3) - 1;
+            oo /= 3;
+          }
+          if (!in_grid(q, h.d, F.n) || cheb(bc, q, h.d) == 0) continue;
+          const int qb = morton_key(q, h.d, F.l);
+          coupled += colour_of(q, h.d) < cb ? F.h_r[qb] : F.h_m[qb];
+        }
+        bytes += 8.0 * (2.0 * n * n + 2.0 * m * coupled);
+      }
     }
+    bytes += 8.0 * 2.0 * (double)h.ntop * h.ntop;
   }
   o->bytes_solve = bytes;
   o->bytes_resident = (double)h.resident;
@@ -473,7 +570,7 @@ aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {
   o->ms_solve = h.ms_solve;
   o->ms_matvec = h.ms_matvec;
   o->kernel_launches = h.nlaunch;
-  for (int g = 0; g < 4; ++g) {
+  for (int g = 0; g < Handle::G_NG; ++g) {
     o->group_ms[g] = h.g_ms[g];
     o->group_flops[g] = h.g_flops[g];
     o->group_launches[g] = h.g_launch[g];
@@ -484,6 +581,7 @@ aifmm_status aifmm_stats(aifmm_h c, aifmm_stats_t* o) {
 aifmm_status aifmm_tree_perm(aifmm_h c, int64_t* perm, int64_t* level_start) {
   if (!c || !perm) return AIFMM_ERR_INVALID;
   Handle& h = c->h;
+  AIFMM_ON_DEVICE(h);
   std::vector<int> p(h.N);
   if (cudaMemcpy(p.data(), h.perm, sizeof(int) * h.N, cudaMemcpyDeviceToHost) != cudaSuccess) return AIFMM_ERR_CUDA;
   for (int64_t i = 0; i < h.N; ++i) perm[i] = p[i];
@@ -507,13 +605,16 @@ aifmm_status aifmm_level_ranks(aifmm_h c, int level, int which, int* ranks) {
   return AIFMM_OK;
 }
 
-aifmm_status aifmm_level_pivots(aifmm_h c, int level, int64_t* pivots) {
+// row pivots (far = false) or far-field pivots (far = true) of every box of a
+// level, concatenated in box order, in the order the search took them
+static aifmm_status level_pivots(aifmm_h c, int level, int64_t* pivots, bool far) {
   if (!c || !pivots) return AIFMM_ERR_INVALID;
   Handle& h = c->h;
   if (level < 2 || level > h.L) return AIFMM_ERR_INVALID;
+  AIFMM_ON_DEVICE(h);
   const NnLevel& N = h.nn[level];
   std::vector<int> p((size_t)N.nb * N.R);
-  if (cudaMemcpy(p.data(), N.pivpos, sizeof(int) * p.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(p.data(), far ? N.far : N.pivpos, sizeof(int) * p.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
     return AIFMM_ERR_CUDA;
   size_t o = 0;
   for (int b = 0; b < N.nb; ++b)
@@ -521,7 +622,17 @@ aifmm_status aifmm_level_pivots(aifmm_h c, int level, int64_t* pivots) {
   return AIFMM_OK;
 }
 
+aifmm_status aifmm_level_pivots(aifmm_h c, int level, int64_t* pivots) {
+  return level_pivots(c, level, pivots, false);
+}
+
+aifmm_status aifmm_level_far_pivots(aifmm_h c, int level, int64_t* pivots) {
+  return level_pivots(c, level, pivots, true);
+}
+
 int aifmm_levels(aifmm_h c) { return c ? c->h.L : 0; }
+
+int aifmm_device(aifmm_h c) { return c ? c->h.device : -1; }
 
 const char* aifmm_last_error(aifmm_h c) {
   if (!c) return g_build_err.c_str();
@@ -531,6 +642,7 @@ const char* aifmm_last_error(aifmm_h c) {
 void aifmm_destroy(aifmm_h c) {
   if (!c) return;
   Handle& h = c->h;
+  DeviceGuard dg(h.device);
   hfree_all(h);
   if (h.own_stream && h.stream) cudaStreamDestroy(h.stream);
   delete c;

@@ -1505,8 +1505,16 @@ static int factor_level(Handle& h, int l) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         dp.begin(phase == 1 ? "qr_basis" : "qrcp_fill");
-        AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, c));
+        delete gt;
+        gt = new GroupTimer(h, Handle::G_QRCP);
+        {
+          Cmp cq = c;
+          cq.flops = h.dacc + 1;   // the pivoted QR's flops are counted apart
+          AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, cq));
+        }
         ++h.nlaunch;
+        delete gt;
+        gt = new GroupTimer(h, Handle::G_COMPRESS);
         dp.end();
         // phase 1 -> project the fill-ins; phase 2 -> the new basis columns
         const int what = phase == 1 ? 0 : 1;
@@ -1772,11 +1780,12 @@ int run_factor(Handle& h) {
     e = factor_level(h, l);
     if (e) return e;
     collect_group_times(h);
-    double fc = 0.0;
-    AIFMM_CUDA_TRY(h, cudaMemcpy(&fc, h.dacc, sizeof(double), cudaMemcpyDeviceToHost));
-    AIFMM_CUDA_TRY(h, cudaMemset(h.dacc, 0, sizeof(double)));
-    h.g_flops[Handle::G_COMPRESS] += fc;
-    h.flops_factor += fc;
+    double fc[2] = {0.0, 0.0};
+    AIFMM_CUDA_TRY(h, cudaMemcpy(fc, h.dacc, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    AIFMM_CUDA_TRY(h, cudaMemset(h.dacc, 0, 2 * sizeof(double)));
+    h.g_flops[Handle::G_COMPRESS] += fc[0];
+    h.g_flops[Handle::G_QRCP] += fc[1];
+    h.flops_factor += fc[0] + fc[1];
     h.flops_factor += level_flops(h, l);
   }
   // top: dense level-1 system in the level-2 multipoles

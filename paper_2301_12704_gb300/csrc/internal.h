@@ -103,10 +103,12 @@ struct Handle {
   bool fma_gemm = false;   // Schur tiles on FP64 FMAs instead of the tensor-core emulation
   bool tc05 = false;       // Schur tiles on tcgen05 (TMEM accumulators) instead of the warp MMAs
   bool fp32 = false;       // FP32 products in the factorisation (preconditioner)
-  enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_NG = 4 };
-  double g_ms[G_NG] = {0, 0, 0, 0};
-  double g_flops[G_NG] = {0, 0, 0, 0};
-  long long g_launch[G_NG] = {0, 0, 0, 0};
+  // kernel groups of the factorisation timed in profile mode; G_QRCP and
+  // G_SCHUR are single kernels (k_cmp_qrcp, k_schur)
+  enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_QRCP = 4, G_NG = 5 };
+  double g_ms[G_NG] = {0, 0, 0, 0, 0};
+  double g_flops[G_NG] = {0, 0, 0, 0, 0};
+  long long g_launch[G_NG] = {0, 0, 0, 0, 0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> g_ev;
   Pts P() const {
     Pts p;

@@ -5,6 +5,7 @@
 // Also the NNCA H^2 product (upward P2M/M2M, M2L, downward L2L/L2P, P2P) and
 // the exact direct-sum product used to measure true residuals.
 #include <algorithm>
+#include <mutex>
 
 #include "dense.cuh"
 #include "internal.h"
@@ -577,10 +578,15 @@ static int sweeps(Handle& h, SolveBufs& B, double* b, int nrhs, int64_t ld) {
   return HOK;
 }
 
-// the gather's shared-memory limit, raised once per device
+// the gather's shared-memory limit, raised once per device; handles are
+// driven from several host threads (many problems, the serving loop), so the
+// per-device flags are guarded
+static std::mutex g_attr_mu;
+
 static int solve_attrs(Handle& h) {
   static bool done[64] = {};
   const int dv = (h.device >= 0 && h.device < 64) ? h.device : 0;
+  std::lock_guard<std::mutex> g(g_attr_mu);
   if (!done[dv]) {
     AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * MAX_GATHER)));
@@ -686,17 +692,26 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLE
 namespace {
 constexpr int kMaxDevices = 64;
 double* g_noalloc_addr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;   // first calls on a device may come from several threads
 }  // namespace
 
 size_t noalloc_scratch_bytes() { return NOALLOC_SCRATCH_DOUBLES * sizeof(double); }
 
-// device address of the array for the current device (host code cannot use
-// the symbol itself); looked up once per device
+// device address of the array on the handle's device (host code cannot use
+// the symbol itself); looked up once per device, with that device current
+// (cudaGetSymbolAddress answers for the current device only)
 static int noalloc_scratch(Handle& h, double** out) {
   if (h.device < 0 || h.device >= kMaxDevices) {
     h.err = "aifmm_solve_noalloc: device index out of range";
     return HINVALID;
   }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h.device) {
+    cudaGetLastError();
+    h.err = "aifmm_solve_noalloc: the handle's device is not the current device";
+    return HINVALID;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
   if (!g_noalloc_addr[h.device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);

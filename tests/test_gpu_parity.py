@@ -1,6 +1,28 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
-the same seeded inputs.  Integer work (tree order, leaf ranges) must match
-exactly; floating-point results within the stated tolerances."""
+the same seeded inputs.
+
+* Integer and index work must match exactly: the tree order and leaf
+  ranges, and the NNCA pivot sets t^{b,i} and s^{b,i} of every box in the
+  order the search took them (Sec. 2.3).  A pivot is the argmax of a
+  floating-point residual, so a box may differ only where the oracle's own
+  record of that search shows the two candidates within rounding of each
+  other (a near-tie), and then every box above it inherits the difference.
+* The ranks after compression (Sec. 3.2, RRQR at eps_A) must equal the
+  oracle's symmetric colour-order elimination, except at directions whose
+  |R_kk| lies at the threshold: the first difference in elimination order
+  must be such a near-tie; later ones may follow from it (they see fill-ins
+  that differ by O(eps_A)), and stay within two directions of threshold
+  decisions.
+* Solutions within 10 eps_A of the oracle (relative 2-norm) and 100 eps_A of
+  a dense LU solve, the tolerance of the method.
+
+Besides five small cases (L <= 3) the file runs three deeper ones: a 2D
+log-kernel problem of 16,384 points at depth 4, a 3D 1/r problem of 4,096
+points at depth 3 (the octree level transition and a top system of about
+4,000 rows, taller than a shared-memory LU panel), and a 2D problem of
+16,384 points with the depth forced to 2 (leaf pivot blocks of more than
+1,024 rows: the tall-panel LU and the blocked multi-launch triangular
+solves)."""
 import numpy as np
 import pytest
 
@@ -25,13 +47,6 @@ def A():
     return lib
 
 
-def _oracle(w, pts, order="colour"):
-    T = Tree(pts, w.leaf)
-    K = Kernel(w.kernel, w.diag, w.length)
-    nn = NNCA(T, K, w.tol)
-    return T, K, nn
-
-
 def _to_orig(T, xt):
     x = np.empty_like(xt)
     x[T.perm] = xt
@@ -43,76 +58,297 @@ def _rel(a, b):
 
 
 CASES = [
-    W.log2d(1024, seed=11, leaf=16, tol=1e-10),
-    W.log2d(1000, seed=12, leaf=16, tol=1e-8),      # ragged occupancy, L=3
-    W.invr2d(1500, seed=13, leaf=24, tol=1e-10),
-    W.gauss2d(900, seed=14, leaf=16, tol=1e-10),
-    W.invr3d(512, seed=15, leaf=8, tol=1e-8),
+    (W.log2d(1024, seed=11, leaf=16, tol=1e-10), None),
+    (W.log2d(1000, seed=12, leaf=16, tol=1e-8), None),      # ragged occupancy, L=3
+    (W.invr2d(1500, seed=13, leaf=24, tol=1e-10), None),
+    (W.gauss2d(900, seed=14, leaf=16, tol=1e-10), None),
+    (W.invr3d(512, seed=15, leaf=8, tol=1e-8), None),
+]
+DEEP = [
+    (W.log2d(16384, seed=21, leaf=64, tol=1e-10, diag=100.0), None),   # L = 4, indefinite (A_ii = 100)
+    (W.invr3d(4096, seed=22, leaf=8, tol=1e-8), None),                   # 3D, L = 3
+    (W.log2d(16384, seed=23, leaf=64, tol=1e-10), 2),                    # depth 2: ~1,024-point leaves
 ]
 
 
-@pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
-def test_tree_and_nnca_match_oracle(A, w):
+def _id(c):
+    w, depth = c
+    return f"{w.name}_s{w.seed}" + (f"_depth{depth}" if depth else "")
+
+
+def _key(w, depth):
+    return (w.name, w.seed, w.diag, w.leaf, w.tol, depth)
+
+
+_NN = {}
+
+
+def _oracle(w, depth):
+    """Oracle tree, kernel and NNCA of one case, computed once."""
+    k = _key(w, depth)
+    if k not in _NN:
+        pts, _ = W.points_and_rhs(w)
+        T = Tree(pts, w.leaf, depth=depth)
+        K = Kernel(w.kernel, w.diag, w.length)
+        _NN[k] = (pts, T, K, NNCA(T, K, w.tol))
+    return _NN[k]
+
+
+_SYM = {}
+
+
+def _oracle_sym(w, depth):
+    """The oracle's symmetric colour-order elimination (reading R13, the
+    GPU's default mode), computed once per case."""
+    k = _key(w, depth)
+    if k not in _SYM:
+        pts, T, K, nn = _oracle(w, depth)
+        _SYM[k] = OF.factor(T, K, nn, w.tol, order="colour", symmetric=True)
+    return _SYM[k]
+
+
+_GEN = {}
+
+
+def _oracle_solution(w, depth, b):
+    """Oracle (general two-sided form, colour order) and dense solutions of
+    a small case, computed once."""
+    k = _key(w, depth)
+    if k not in _GEN:
+        pts, T, K, nn = _oracle(w, depth)
+        xo = _to_orig(T, OF.solve(OF.factor(T, K, nn, w.tol, order="colour"), b[T.perm]))
+        _GEN[k] = (xo, np.linalg.solve(K.dense(pts), b))
+    return _GEN[k]
+
+
+def _build(A, w, depth, **kw):
     pts, _ = W.points_and_rhs(w)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length)
-    T, K, nn = _oracle(w, pts)
+    return A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, depth=depth or 0, **kw)
+
+
+# ---------------------------------------------------------------- pivots
+
+# A decision between two candidates counts as a near-tie when their residual
+# magnitudes differ by at most TIE times the magnitude of the unreduced row
+# (or column) they were computed from: the residual entries carry rounding
+# errors of a few units in the last place of that magnitude per ACA step.
+TIE = 1e-11
+# The stopping test |u||v| <= eps ||S||_F compares a product of residual
+# norms whose entries are eps-sized remnants of O(1) entries: its two sides
+# carry relative rounding errors of about u / eps.
+STOP_TIE = 1e-3
+
+
+def _explain(nn, l, b, g_rows, g_far):
+    """Why the GPU's pivot search of box b at level l may differ from the
+    oracle's: the first differing decision, taken from the oracle's record
+    of the search, must be a near-tie.  Returns a description or None."""
+    rows, cols, tr = nn.trace_box(l, b)
+    pos_r = {int(p): i for i, p in enumerate(rows)}
+    pos_c = {int(p): j for j, p in enumerate(cols)}
+    gi = [pos_r.get(int(p), -1) for p in g_rows]
+    gj = [pos_c.get(int(p), -1) for p in g_far]
+    if -1 in gi or -1 in gj:
+        return None                                   # a pivot outside the search sets
+    kept = [r for r in tr if not r.get("stopped")]
+    stop = tr[-1] if tr and tr[-1].get("stopped") else None
+    for k in range(max(len(kept), len(gi)) + 1):
+        if k < len(kept) and k < len(gi):
+            rec = kept[k]
+            if gi[k] != rec["row"]:
+                if k == 0:
+                    return None                       # both start at row 0
+                prev = kept[k - 1]
+                a = prev["col_abs"]
+                if a[gi[k]] < 0:
+                    return None                       # a row already used
+                gap = a[rec["row"]] - a[gi[k]]
+                return f"row tie at step {k} (gap {gap:.2e})" if gap <= TIE * prev["col_scale"] else None
+            if gj[k] != rec["col"]:
+                a = rec["row_abs"]
+                if a[gj[k]] < 0:
+                    return None
+                gap = a[rec["col"]] - a[gj[k]]
+                return f"column tie at step {k} (gap {gap:.2e})" if gap <= TIE * rec["row_scale"] else None
+            continue
+        if len(gi) == len(kept):
+            return None                               # equal sequences: nothing to explain
+        if len(gi) < len(kept):
+            # the GPU stopped at step k, the oracle kept the term
+            rec = kept[k]
+            ratio = rec["stop_lhs"] / rec["stop_rhs"]
+            return f"stop tie at step {k} (ratio {ratio:.6f})" if ratio <= 1 + STOP_TIE else None
+        # the oracle stopped at step k, the GPU kept the term
+        if stop is None or len(kept) != k:
+            return None
+        ratio = stop["stop_lhs"] / stop["stop_rhs"]
+        return f"stop tie at step {k} (ratio {ratio:.6f})" if ratio >= 1 - STOP_TIE else None
+    return None
+
+
+def _compare_pivots(A, h, T, nn):
+    """Every box's pivot sequences, level L first.  Returns (equal, ties,
+    inherited, the set of differing boxes)."""
+    equal = ties = inherited = 0
+    diff = set()
+    notes = []
+    for l in range(T.L, 1, -1):
+        rg = A.aifmm_level_ranks(h, l, 0)
+        pg = A.aifmm_level_pivots(h, l)
+        fg = A.aifmm_level_far_pivots(h, l)
+        off = np.concatenate([[0], np.cumsum(rg)])
+        for b in range(T.nboxes(l)):
+            gr, gf = pg[off[b]:off[b + 1]], fg[off[b]:off[b + 1]]
+            if np.array_equal(gr, nn.piv[l][b]) and np.array_equal(gf, nn.far[l][b]):
+                equal += 1
+                continue
+            diff.add((l, b))
+            if l < T.L and any((l + 1, c) in diff for c in T.children(b)):
+                inherited += 1                       # its rows are other pivots already
+                continue
+            why = _explain(nn, l, b, gr, gf)
+            assert why is not None, (
+                f"level {l} box {b}: pivots differ without a near-tie\n gpu rows {list(gr)}\n"
+                f" oracle   {list(nn.piv[l][b])}\n gpu far  {list(gf)}\n oracle   {list(nn.far[l][b])}")
+            ties += 1
+            notes.append(f"l{l} b{b}: {why}")
+    return equal, ties, inherited, diff, notes
+
+
+@pytest.mark.parametrize("case", CASES + DEEP, ids=_id)
+def test_tree_and_pivots_match_oracle(A, case):
+    w, depth = case
+    pts, T, K, nn = _oracle(w, depth)
+    h = _build(A, w, depth)
     perm, starts = A.aifmm_tree_perm(h)
     assert A.aifmm_levels(h) == T.L
     assert np.array_equal(perm, T.perm)                      # bit-exact
     assert np.array_equal(starts, T.start[T.L])
-    same = 0
-    total = 0
-    for l in range(2, T.L + 1):
-        r = A.aifmm_level_ranks(h, l, 0)
-        ro = np.array([nn.rank[l][b] for b in range(T.nboxes(l))])
-        total += len(ro)
-        same += int((r == ro).sum())
-    # pivots are floating-point decisions (argmax of residuals); allow a rare
-    # near-tie to differ, but the bulk must be identical
-    assert same >= 0.97 * total, (same, total)
+    equal, ties, inherited, diff, notes = _compare_pivots(A, h, T, nn)
+    total = equal + ties + inherited
+    print(f"{_id(case)}: {equal}/{total} boxes equal, {ties} near-ties, {inherited} inherited; " + "; ".join(notes))
+    # near-ties are rare events: the bulk of the index work is identical
+    assert equal >= 0.9 * total, (equal, total, notes)
+    A.aifmm_destroy(h)
 
 
-_ORACLE_X = {}
+# ---------------------------------------------------------------- ranks
+
+def _contested(rec, rg):
+    """|R_kk| / tau of the directions on which the GPU's rank rg and the
+    oracle's rank disagree (the oracle's record of the box's RRQR)."""
+    ro, d, tau = rec["rank"], rec["rdiag"], rec["tau"]
+    lo, hi = min(rg, ro), max(rg, ro)
+    vals = [d[k] / tau for k in range(lo, min(hi, len(d)))]
+    if hi > len(d):
+        return None                                   # the GPU kept more directions than exist
+    return vals
 
 
-def _oracle_solution(w, pts, b):
-    """Oracle (colour order) and dense solutions of one case, computed once."""
-    if w.name not in _ORACLE_X:
-        T, K, nn = _oracle(w, pts)
-        xo = _to_orig(T, OF.solve(OF.factor(T, K, nn, w.tol, order="colour"), b[T.perm]))
-        _ORACLE_X[w.name] = (xo, np.linalg.solve(K.dense(pts), b))
-    return _ORACLE_X[w.name]
+@pytest.mark.parametrize("case", CASES + DEEP, ids=_id)
+def test_compressed_ranks_match_oracle(A, case):
+    """Ranks after every box's compress-and-redirect, in elimination order,
+    against the oracle's symmetric colour-order elimination."""
+    w, depth = case
+    pts, T, K, nn = _oracle(w, depth)
+    h = _build(A, w, depth)
+    _, _, _, diff, _ = _compare_pivots(A, h, T, nn)
+    if diff:
+        pytest.skip(f"NNCA pivots differ by near-ties in {len(diff)} boxes; the operators differ")
+    A.aifmm_factor(h)
+    F = _oracle_sym(w, depth)
+    first = None
+    n = same = 0
+    worst = []
+    for l in range(T.L, 1, -1):
+        rg = A.aifmm_level_ranks(h, l, 1)
+        for b in T.order(l, "colour"):
+            ro = F.ranks[(l, b)]
+            n += 1
+            if int(rg[b]) == ro:
+                same += 1
+                continue
+            rec = F.rrqr.get((l, b))
+            assert rec is not None, f"level {l} box {b}: rank {rg[b]} vs {ro} with no compression in the oracle"
+            vals = _contested(rec, int(rg[b]))
+            assert vals is not None, (l, b, int(rg[b]), ro)
+            worst.append((l, b, int(rg[b]), ro, [round(v, 4) for v in vals]))
+            if first is None:
+                first = worst[-1]
+                # the first difference: a direction at the threshold, to rounding
+                assert abs(int(rg[b]) - ro) == 1 and abs(vals[0] - 1.0) <= 0.05, first
+            # later ones: at most two directions, each near the threshold
+            assert abs(int(rg[b]) - ro) <= 2 and all(0.25 <= v <= 4.0 for v in vals), worst[-1]
+    print(f"{_id(case)}: {same}/{n} ranks equal; differences (level, box, gpu, oracle, |R_kk|/tau): {worst}")
+    assert same >= 0.9 * n, (same, n, worst)
+    A.aifmm_destroy(h)
 
+
+# ---------------------------------------------------------------- solutions
 
 @pytest.mark.parametrize("symmetric,mode", [(True, "mma"), (False, "mma"), (True, "fma"), (True, "tcgen05")],
                          ids=["sym", "general", "sym-fp64fma", "sym-tcgen05"])
-@pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
-def test_factor_solve_matches_oracle(A, w, symmetric, mode):
+@pytest.mark.parametrize("case", CASES, ids=_id)
+def test_factor_solve_matches_oracle(A, case, symmetric, mode):
     """Both elimination modes, and the Schur tiles on the warp MMAs, on
     tcgen05 or on FP64 FMAs, against the oracle's general elimination: they
     differ from it only by rounding and the RRQR cut-off, so the same 10 tol
     bound holds."""
+    w, depth = case
     pts, b = W.points_and_rhs(w, nrhs=2)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, symmetric=symmetric,
-                      fma_gemm=mode == "fma", tcgen05=mode == "tcgen05")
+    h = _build(A, w, depth, symmetric=symmetric, fma_gemm=mode == "fma", tcgen05=mode == "tcgen05")
     A.aifmm_factor(h)
     x = A.aifmm_solve(h, b)
-    xo, xd = _oracle_solution(w, pts, b)
+    xo, xd = _oracle_solution(w, depth, b)
     assert _rel(x, xo) <= 10 * w.tol
     assert _rel(x, xd) <= 100 * w.tol
+    A.aifmm_destroy(h)
+
+
+@pytest.mark.parametrize("symmetric", [True, False], ids=["sym", "general"])
+@pytest.mark.parametrize("case", DEEP, ids=_id)
+def test_deep_factor_solve_matches_oracle(A, case, symmetric):
+    """The deeper cases, both elimination modes, against the oracle's
+    symmetric colour-order elimination (10 eps_A); the 3D case also against
+    a dense solve.  The structure each case is there for is checked too."""
+    w, depth = case
+    pts, T, K, nn = _oracle(w, depth)
+    _, b = W.points_and_rhs(w, nrhs=2)
+    h = _build(A, w, depth, symmetric=symmetric)
+    A.aifmm_factor(h)
+    st = A.aifmm_stats(h)
+    if w.dim == 3:
+        assert st["levels"] == 3 and st["top_size"] > 1000          # octree transition; tall top LU
+    elif depth == 2:
+        assert st["levels"] == 2 and st["max_m"] > 1024             # pivot blocks over 1,024 rows
+    else:
+        assert st["levels"] == 4
+    x = A.aifmm_solve(h, b)
+    F = _oracle_sym(w, depth)
+    xo = _to_orig(T, OF.solve(F, b[T.perm]))
+    rel = _rel(x, xo)
+    assert rel <= 10 * w.tol, rel
+    if w.n <= 4096:
+        xd = np.linalg.solve(K.dense(pts), b)
+        assert _rel(x, xd) <= 100 * w.tol
+    # one right-hand side (the one-launch small solve) against the same
+    x1 = A.aifmm_solve(h, b[:, :1])
+    assert _rel(x1[:, 0], xo[:, 0]) <= 10 * w.tol
+    A.aifmm_destroy(h)
 
 
 def test_h2_matvec_matches_oracle(A):
-    w = CASES[0]
+    w, depth = CASES[0]
     pts, b = W.points_and_rhs(w, nrhs=3)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf)
+    h = _build(A, w, depth)
     y = A.aifmm_matvec(h, b)
-    T, K, nn = _oracle(w, pts)
+    _, T, K, nn = _oracle(w, depth)
     yo = _to_orig(T, OH.matvec(T, K, nn, b[T.perm]))
     assert _rel(y, yo) < 1e-11
     yd = A.aifmm_direct_matvec(h, b)
     ye = K.dense(pts) @ b
     assert _rel(yd, ye) < 1e-13
+    A.aifmm_destroy(h)
 
 
 def test_small_config_full_size(A):
@@ -123,18 +359,19 @@ def test_small_config_full_size(A):
     h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf)
     A.aifmm_factor(h)
     x = A.aifmm_solve(h, b)[:, 0]
-    T, K, nn = _oracle(w, pts)
+    _, T, K, nn = _oracle(w, None)
     xo = _to_orig(T, OF.solve(OF.factor(T, K, nn, w.tol, order="colour"), b[T.perm, 0]))
     rel = _rel(x, xo)
     assert rel <= 10 * w.tol, rel
     xd = np.linalg.solve(K.dense(pts), b[:, 0])
     assert _rel(x, xd) <= 1e-8
+    A.aifmm_destroy(h)
 
 
 def test_state_and_argument_errors(A):
-    w = CASES[0]
+    w, depth = CASES[0]
     pts, b = W.points_and_rhs(w)
-    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf)
+    h = _build(A, w, depth)
     with pytest.raises(A.AifmmError) as e:
         A.aifmm_solve(h, b)
     assert e.value.status == 4
