@@ -56,7 +56,13 @@ Readings where the paper is silent or ambiguous:
   columns U_b are taken first, in order (so U_b = U~_b L_b holds to rounding,
   as the paper's eq. P2P_2a requires), followed by pivoting on the largest
   residual column norm among the fill-in columns; fill-in directions are kept
-  while |R_kk| > eps_A * max_j ||F_:j||.
+  while |R_kk| > eps_A * max_j ||[U_b | F]_:j||: the paper asks for a
+  relative residual O(eps_A) of the decomposition of the augmented matrix
+  [U_b | F] (Sec. 3.2.1), so the scale is that of the augmented matrix, basis
+  columns included.  (Measured against the fill-in columns alone, fill-ins
+  that are rounding noise next to the basis -- A_ii = N makes them ~1e-17 of
+  it -- were kept to ten digits of their own size: ranks followed the
+  rounding.)
 * R4 equal ranks: the pivot [[K, U],[V^T, 0]] is square only if U_b and V_b
   have equal column counts; both sides keep r' = max(r'_U, r'_V) columns.
   The smaller side is extended by the other side's extra basis columns,
@@ -114,6 +120,11 @@ def qrcp_forced(M: np.ndarray, nf: int):
         A[k:, k:] -= 2.0 * np.outer(v, v @ A[k:, k:])
         Q[:, k:] -= 2.0 * np.outer(Q[:, k:] @ v, v)
     return Q, rdiag
+
+
+def _colmax(M: np.ndarray) -> float:
+    """Largest column 2-norm of M (0 for no columns)."""
+    return float(np.linalg.norm(M, axis=0).max()) if M.shape[1] else 0.0
 
 
 def rrqr_rank(rdiag, nf: int, tau: float) -> int:
@@ -211,13 +222,14 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool 
     # ---- RRQR on both sides (R3) and equal ranks (R4)
     QU, dU = qrcp_forced(np.hstack([U, Frow]), r)
     QV, dV = (QU, dU) if symmetric else qrcp_forced(np.hstack([V, Fcol]), r)
-    tauU = eps * (np.linalg.norm(Frow, axis=0).max() if Frow.shape[1] else 0.0)
-    tauV = eps * (np.linalg.norm(Fcol, axis=0).max() if Fcol.shape[1] else 0.0)
+    tauU = eps * max(_colmax(U), _colmax(Frow))
+    tauV = eps * max(_colmax(V), _colmax(Fcol))
     rU = rrqr_rank(dU, r, tauU)
     rV = rU if symmetric else rrqr_rank(dV, r, tauV)
     rn = max(rU, rV)
     if log is not None:
-        log[(l, b)] = {"r_old": r, "rdiag": np.array(dU), "tau": tauU, "rank": rn}
+        log[(l, b)] = {"r_old": r, "rdiag": np.array(dU), "tau": tauU, "rank": rn, "m": m,
+                       "ncols": Frow.shape[1], "partners": list(wcols)}
     assert rn <= m
     if rn == 0:
         # every fill-in column is exactly zero: drop them
@@ -347,10 +359,10 @@ def _set_col_basis(S: BlockSystem, T, l: int, b: int, Vt: np.ndarray) -> np.ndar
 def _grow(Q0: np.ndarray, F: np.ndarray, eps: float) -> np.ndarray:
     """RRQR of [Q0 | F] with Q0's columns taken first (reading R3): the
     orthonormal basis of Q0 plus the directions of F kept above
-    eps * max_j ||F_:j||."""
+    eps * max_j ||[Q0 | F]_:j||."""
     r = Q0.shape[1]
     Q, d = qrcp_forced(np.hstack([Q0, F]), r)
-    tau = eps * (np.linalg.norm(F, axis=0).max() if F.shape[1] else 0.0)
+    tau = eps * max(_colmax(Q0), _colmax(F))
     return Q[:, :rrqr_rank(d, r, tau)]
 
 

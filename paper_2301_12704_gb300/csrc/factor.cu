@@ -209,8 +209,8 @@ struct Cmp {
   int* skip;           // [cnt] 1 if nothing is pending
   double* Lm;          // [cnt][2][R*R] L_b (side 0), R_b (side 1), ld R
   double* T;           // [cnt][2][R*WC] Q0^T X of the projections, ld R
-  double* tau;         // [cnt][2] max_j ||F_j||^2 of the fill-in columns (bit pattern, atomicMax);
-                       // the RRQR threshold is eps * sqrt of it
+  double* tau;         // [cnt][2] max_j ||[U_b | F]_j||^2 over the basis and fill-in columns
+                       // (bit pattern, atomicMax); the RRQR threshold is eps * sqrt of it
   int phase;           // k_cmp_qrcp: 1 = QR of the basis columns, 2 = QRCP of the projected fill-ins
   int ccap;            // k_cmp_qrcp: column capacity of the phase (shared-memory norms)
   double eps;
@@ -300,9 +300,11 @@ __global__ void k_cmp_list(LV v, Cmp c, int nsides) {
 
 // gather [U_b | row fill-ins] (side 0) and [V_b | column fill-ins^T] (side 1)
 // into W; blockIdx.y = 0 copies the basis, blockIdx.y = 1 + s the pending
-// block of stencil slot s, and takes the largest squared norm of its columns
-// into the threshold accumulator (non-negative doubles order as their bit
-// patterns).  grid (cnt * sides, ns5 + 1)
+// block of stencil slot s; each takes the largest squared norm of its
+// columns into the threshold accumulator (non-negative doubles order as
+// their bit patterns): the RRQR's residual is relative to the augmented
+// matrix [U_b | F] (Sec. 3.2.1), basis columns included.
+// grid (cnt * sides, ns5 + 1)
 __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
   __shared__ WsBlk sw;
   __shared__ double shm[8];
@@ -310,28 +312,31 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
   const int b = cbox(c, v, t);
   const int mb = v.m[b], rb = c.rold[t];
   double* W = c.W + ((size_t)t * 2 + side) * v.M * c.WC;
+  int off, ncol;
   if (blockIdx.y == 0) {
     const double* base = side == 0 ? v.u(b) : v.v(b);
     for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
       int i = e % mb, j = e / mb;
       W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
     }
-    return;
-  }
-  const int sl = blockIdx.y - 1;
-  const int off = c.boff[((size_t)t * 2 + side) * v.ns5 + sl];
-  if (off < 0) return;
-  if (threadIdx.x == 0) sw = ws_block(v, b, sl, side, c.col);
-  __syncthreads();
-  const WsBlk w = sw;
-  for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
-    int i = e % w.rows, j = e / w.rows;
-    if (side == 0) W[i + (size_t)(off + j) * v.M] = w.src[i + (size_t)j * w.ld];
-    else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
+    off = 0;
+    ncol = rb;
+  } else {
+    const int sl = blockIdx.y - 1;
+    off = c.boff[((size_t)t * 2 + side) * v.ns5 + sl];
+    if (off < 0) return;
+    if (threadIdx.x == 0) sw = ws_block(v, b, sl, side, c.col);
+    __syncthreads();
+    const WsBlk w = sw;
+    for (int e = threadIdx.x; e < w.rows * w.cols; e += blockDim.x) {
+      int i = e % w.rows, j = e / w.rows;
+      if (side == 0) W[i + (size_t)(off + j) * v.M] = w.src[i + (size_t)j * w.ld];
+      else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
+    }
+    ncol = side == 0 ? w.cols : w.rows;
   }
   __syncthreads();
   // largest squared column norm of the copied columns (m_b rows each)
-  const int ncol = side == 0 ? w.cols : w.rows;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   double mx = 0.0;
   for (int j = wp; j < ncol; j += 8) {
@@ -348,7 +353,7 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
     double a = 0.0;
     for (int q = 0; q < 8; ++q) a = fmax(a, shm[q]);
     atomicMax(reinterpret_cast<unsigned long long*>(c.tau + t * 2 + side), (unsigned long long)__double_as_longlong(a));
-    atomicAdd(c.flops, 2.0 * mb * (double)ncol);
+    if (blockIdx.y > 0) atomicAdd(c.flops, 2.0 * mb * (double)ncol);
   }
 }
 
@@ -369,8 +374,9 @@ __global__ void k_cmp_skip(LV v, Cmp c) {
 //            fill-in column);
 //   phase 2  Householder QR with column pivoting of the projected F: the
 //            largest residual column while its norm exceeds
-//            tau = eps * max_j ||F_j|| (norms of the fill-ins before the
-//            projection, k_cmp_gather); Q' = Q[:, nf:rank], then made orthogonal
+//            tau = eps * max_j ||[U_b | F]_j|| (the column norms of the
+//            augmented matrix before the projection, k_cmp_gather: the
+//            relative residual of Sec. 3.2.1); Q' = Q[:, nf:rank], then made orthogonal
 //            to Q0 once more (the projection leaves Q0 components of size
 //            u ||F_j|| / |R_kk|).
 // Produces Q[:, :rank] explicitly, rank = nf + (phase-2 columns).

@@ -14,8 +14,10 @@ X_q of the uneliminated leaf boxes and a everything else.  So:
 * with threshold 0 every direction of [U_b | fill-ins] is kept and the
   redirect is exact: G is unchanged to rounding;
 * with threshold eps_A the discarded directions have R_kk <= eps_A times the
-  largest fill-in column, so G changes by O(eps_A |F|), |F| the Frobenius
-  norm of the fill-ins that were compressed.
+  largest column of the augmented matrix [U_b | fill-ins] (the relative
+  residual of its RRQR, Sec. 3.2.1), so G changes by O(eps_A |[U | F]|),
+  |[U | F]| the Frobenius norm of the bases and fill-ins that were
+  compressed.
 
 The diagonal is 20 rather than N so that the fill-ins are not negligible
 against the rounding of G (with A_ii = N they are ~1e-12 of |G|).
@@ -76,8 +78,11 @@ def state():
     keep_r, keep_c = [("X", b) for b in live], [("x", b) for b in live]
     rs, cs, wcols, wrows = _pending(S, T, L, target)
     nF = float(np.hypot(np.linalg.norm(S.dense(rs, wcols)), np.linalg.norm(S.dense(wrows, cs))))
+    zb, Yb = ("z", L, target), ("Y", L, target)
+    nU = float(np.hypot(np.linalg.norm(S.dense(rs, [zb])), np.linalg.norm(S.dense([Yb], cs))))
     G0 = _reduced(S, keep_r, keep_c)
-    return dict(S=S, T=T, L=L, b=target, m=T.count(L, target), keep=(keep_r, keep_c), G0=G0, nF=nF)
+    return dict(S=S, T=T, L=L, b=target, m=T.count(L, target), keep=(keep_r, keep_c), G0=G0, nF=nF,
+                nA=float(np.hypot(nF, nU)))
 
 
 def _redirect(st, eps, grouping):
@@ -105,5 +110,5 @@ def test_truncated_redirect_changes_the_operator_by_order_eps(state, grouping):
     d0, r0 = _redirect(state, 0.0, grouping)
     dG, r = _redirect(state, eps, grouping)
     assert r < r0                      # directions were discarded
-    assert dG <= 10.0 * eps * state["nF"], (dG, eps * state["nF"])
+    assert dG <= 10.0 * eps * state["nA"], (dG, eps * state["nA"])
     assert dG >= 10.0 * d0             # the truncation is visible above rounding
