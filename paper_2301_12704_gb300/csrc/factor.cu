@@ -1148,22 +1148,55 @@ __device__ inline double* schur_target(const LV& v, int rbox, int rtype, int cty
   return ctype == 0 ? v.lx(rbox, slot5(pc, qc, v.d)) : v.ly(rbox, slot6(pc, qc, v.d));
 }
 
-// Schur update of every coupled block; 64x64 tiles.
-// grid (MAXC * tpb, MAXC * tpb, cnt) with tpb = tiles per block side.
+// One work item of the Schur update: box t of the colour, coupled row entity
+// ri and column entity cj, and the 64 x 64 output tile (ti, tj) of their
+// block; rc = ri | cj << 8 | ti << 16 | tj << 24.
+struct SchurItem {
+  int t, rc;
+};
+
+// The Schur update's work list: for every box of the colour, the (row
+// entity, column entity, tile) combinations that exist -- i <= j only with
+// sym -- appended to one list (one thread per box, one atomicAdd per box on
+// the list's counter, which the caller cleared).  Boxes of one colour update
+// disjoint blocks, so the order of the list does not matter.
+__global__ void k_schur_items(Elim e, int sym, SchurItem* __restrict__ items, int* __restrict__ count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= e.cnt) return;
+  const Coupled* R = e.rows + (size_t)t * MAXC;
+  const Coupled* C = e.cols + (size_t)t * MAXC;
+  const int nr = e.nrow[t], nc = e.ncol[t];
+  int n = 0;
+  for (int ri = 0; ri < nr; ++ri)
+    for (int cj = sym ? ri : 0; cj < nc; ++cj) n += ((R[ri].size + 63) / 64) * ((C[cj].size + 63) / 64);
+  int o = atomicAdd(count, n);
+  for (int ri = 0; ri < nr; ++ri)
+    for (int cj = sym ? ri : 0; cj < nc; ++cj) {
+      const int tr = (R[ri].size + 63) / 64, tc = (C[cj].size + 63) / 64;
+      for (int ti = 0; ti < tr; ++ti)
+        for (int tj = 0; tj < tc; ++tj) {
+          SchurItem it;
+          it.t = t;
+          it.rc = ri | (cj << 8) | (ti << 16) | (tj << 24);
+          items[o++] = it;
+        }
+    }
+}
+
+// Schur update of one item (one 64 x 64 output tile of one coupled block).
 // The row and column lists name the same entities in the same order
 // (X_p <-> x_p, Lc_p <-> y_p, Lc_b <-> y_b), so with sym (A = A^T, which the
 // elimination keeps: Piv and the Schur complement stay symmetric) the block
-// (j, i) is the transpose of (i, j): only i <= j is computed and each
+// (j, i) is the transpose of (i, j): only i <= j is listed and each
 // off-diagonal tile is also stored transposed at its mirror.
 // PM: the tile product mode (dense.cuh): FP64 FMAs, the BF16 warp MMAs or
-// tcgen05 in FP64 precision, or FP32.
+// tcgen05 in FP64 precision, or FP32.  Every thread of the CTA runs it with
+// the same item (the tiles synchronise the CTA).
 template <int PM>
-__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
-  int t = blockIdx.z;
-  int ri = blockIdx.y / tpb, ti = blockIdx.y % tpb;
-  int cj = blockIdx.x / tpb, tj = blockIdx.x % tpb;
-  if (ri >= e.nrow[t] || cj >= e.ncol[t]) return;
-  if (sym && ri > cj) return;
+__device__ __forceinline__ void schur_tile(const LV& v, const Elim& e, const SchurItem item, int sym,
+                                           unsigned char* ozs) {
+  const int t = item.t;
+  const int ri = item.rc & 0xff, cj = (item.rc >> 8) & 0xff, ti = (item.rc >> 16) & 0xff, tj = item.rc >> 24;
   Coupled R = e.rows[(size_t)t * MAXC + ri];
   Coupled C = e.cols[(size_t)t * MAXC + cj];
   int i0 = ti * 64, j0 = tj * 64;
@@ -1191,12 +1224,9 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
   const double* A = R.type == 0 ? v.xx(R.box, sp) : v.lx(R.box, sp);
   int lda = R.type == 0 ? v.M : v.R;
   if (PM == PM_TC05) {
-    extern __shared__ __align__(16) unsigned char ozs[];
     tile_gemm_64_tc(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs, e.err);
   } else if (PM == PM_OZ) {
-    extern __shared__ __align__(16) unsigned char ozs[];
     tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
-
   } else if (PM == PM_F32) {
     tile_gemm_64<float>(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   } else {
@@ -1219,6 +1249,26 @@ __global__ void __launch_bounds__(256) k_schur(LV v, Elim e, int tpb, int sym) {
     }
     if (threadIdx.x == 0 && ti == 0 && tj == 0 && ws)
       atomicOr(v.flag + (size_t)C.box * v.ns5 + slot5(qc, pc, v.d), C.type == 0 ? 1u : 2u);
+  }
+}
+
+// Schur update of every coupled block over the colour's work list.
+// Persistent: each CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+// (grid: the CTAs resident on the device at once), except for the tcgen05
+// tile, whose tensor-memory allocation a CTA may make once: there the grid
+// covers an upper bound of the list and each CTA takes at most one item.
+template <int PM>
+__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, const SchurItem* __restrict__ items,
+                                              const int* __restrict__ count, int sym) {
+  extern __shared__ __align__(16) unsigned char ozs[];
+  const int n = *count;
+  if (PM == PM_TC05) {
+    if ((int)blockIdx.x < n) schur_tile<PM>(v, e, items[blockIdx.x], sym, ozs);
+    return;
+  }
+  for (int g = blockIdx.x; g < n; g += gridDim.x) {
+    schur_tile<PM>(v, e, items[g], sym, ozs);
+    __syncthreads();   // the tile's shared memory is reused by the next item
   }
 }
 
@@ -1269,6 +1319,26 @@ __global__ void k_xoff(int nb, int d, const int* __restrict__ r, int* __restrict
 // (unless tcgen05 is chosen there) and, with PM_F32, of the Z solve and the
 // pivot LU's trailing updates
 static int product_mode(const Handle& h) { return h.fp32 ? PM_F32 : h.fma_gemm ? PM_FMA : PM_OZ; }
+
+// CTAs of the persistent Schur kernel that fit on one SM at once, per
+// product mode (queried once per handle)
+static int schur_ctas_per_sm(Handle& h, int pm) {
+  static thread_local int cache[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  (void)h;
+  if (pm < 0 || pm >= 8) return 1;
+  if (!cache[pm]) {
+    int nb = 0;
+    cudaError_t e = pm == PM_OZ   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_OZ>, 256, OZ_SMEM)
+                    : pm == PM_F32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_F32>, 256, 0)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_FMA>, 256, 0);
+    if (e != cudaSuccess || nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    cache[pm] = nb;
+  }
+  return cache[pm];
+}
 
 static int alloc_level(Handle& h, FacLevel& F) {
   const size_t nb = F.nb;
@@ -1677,11 +1747,21 @@ static int factor_level(Handle& h, int l) {
     gt = new GroupTimer(h, Handle::G_SCHUR);
     dp.begin("schur");
     {
-      const dim3 g(MAXC * tpb, MAXC * tpb, cnt);
-      if (pm == PM_OZ && h.tc05)
-        k_schur<PM_TC05><<<g, 256, TC_SMEM, st>>>(v, e, tpb, h.sym ? 1 : 0);
-      else
-        AIFMM_LAUNCH_PM(pm, k_schur, g, v, e, tpb, h.sym ? 1 : 0);
+      // the work list: at most (3^d + 1)^2 entity pairs of tpb^2 tiles per box
+      const int ne = ipow(3, d) + 1;
+      const size_t cap = (size_t)cnt * ne * ne * tpb * tpb;
+      SchurItem* items = (SchurItem*)hscratch(h, 35, sizeof(SchurItem) * cap);
+      int* nitems = (int*)hscratch(h, 36, sizeof(int));
+      if (!items || !nitems) return HOOM;
+      AIFMM_CUDA_TRY(h, cudaMemsetAsync(nitems, 0, sizeof(int), st));
+      k_schur_items<<<(cnt + 127) / 128, 128, 0, st>>>(e, h.sym ? 1 : 0, items, nitems); ++h.nlaunch;
+      const int sym = h.sym ? 1 : 0;
+      if (pm == PM_OZ && h.tc05) {
+        k_schur<PM_TC05><<<(unsigned)cap, 256, TC_SMEM, st>>>(v, e, items, nitems, sym);
+      } else {
+        const int g = h.nsm * schur_ctas_per_sm(h, pm);
+        AIFMM_LAUNCH_PM(pm, k_schur, g, v, e, items, nitems, sym);
+      }
     }
     ++h.nlaunch;
     dp.end();
