@@ -169,6 +169,18 @@ __host__ __device__ inline int colour_box(int col, int t, int d, int l) {
   return morton_key(c, d, l);
 }
 
+// index of the box with coordinates c among the boxes of its colour on an
+// n^d grid (the inverse of colour_box)
+__host__ __device__ inline int colour_index(const int* c, int d, int n) {
+  int t = 0, stride = 1;
+  for (int k = 0; k < d; ++k) {
+    const int ck = c[k] % 3;
+    t += (c[k] / 3) * stride;
+    stride *= (n - ck + 2) / 3;
+  }
+  return t;
+}
+
 // ---- reductions -------------------------------------------------------------
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -909,6 +909,98 @@ __global__ void __launch_bounds__(256) k_cmp_col_transform(LV v, Cmp c) {
   }
 }
 
+// Symmetric mode (A = A^T, V~_b = U~_b): the column side of the compression
+// as transposes of the row side's results, which hold them already --
+//   A_db R_b^T      = (L_b A_bd)^T            for d in the window of b,
+//   P2L_qb V~ added = (U~^T M2P_bq)^T added   (q eliminated: part of A_qb),
+//   M2P_qb = P2P_qb V~ = (P2L_bq)^T           (q not yet eliminated),
+//   V^dag_b         = U^dag_b,
+// except where both boxes of a block are compressed in this step (the
+// diagonal block A_bb, and M2L blocks between two boxes of the colour): the
+// block needs both transforms, and takes the product with R_b^T here after
+// its row box's transform.  Runs after the row side (k_cmp_row_done,
+// k_cmp_set_rank) and before k_cmp_col_done; replaces k_cmp_col_transform
+// and k_cmp_col_fill.  grid (ns6 + 1 + ns5, cnt): window slots, V^dag, and
+// stencil slots of the pending column-side blocks.
+__global__ void __launch_bounds__(256) k_cmp_col_mirror(LV v, Cmp c) {
+  __shared__ double row[TR_CG][1024];
+  __shared__ WsBlk sw;
+  const int x = blockIdx.x, t = blockIdx.y;
+  if (c.skip[t]) return;
+  const int b = cbox(c, v, t);
+  const int rn = c.rn[t], ro = c.rold[t];
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  if (x < v.ns6) {
+    slot6_coords(bc, x, v.d, q);   // d in the window of b  <=>  b in the window of d
+    if (!in_grid(q, v.d, v.n)) return;
+    const int db = morton_key(q, v.d, v.l);
+    double* blk = v.ly(db, slot6(q, bc, v.d));
+    const int nrows = v.r[db];
+    bool both = db == b;
+    if (!both && colour_of(q, v.d) == c.col) both = !c.skip[colour_index(q, v.d, v.n)];
+    if (!both) {
+      // A_db := (A_bd)^T, r_db x rn
+      const double* src = v.ly(b, x);
+      for (int e = threadIdx.x; e < nrows * rn; e += blockDim.x) {
+        const int i = e % nrows, j = e / nrows;
+        blk[i + (size_t)j * v.R] = src[j + (size_t)i * v.R];
+      }
+      return;
+    }
+    // blk[0..nrows, 0..rn) := blk[.., 0..ro) R_b^T, TR_CG rows at a time
+    const double* Rm = c.Lm + ((size_t)t * 2 + 1) * v.R * v.R;
+    for (int i0 = 0; i0 < nrows; i0 += TR_CG) {
+      const int ni = min(TR_CG, nrows - i0);
+      for (int e = threadIdx.x; e < TR_CG * ro; e += blockDim.x) {
+        const int u = e / ro, p = e % ro;
+        row[u][p] = u < ni ? blk[(i0 + u) + (size_t)p * v.R] : 0.0;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < rn; j += blockDim.x) {
+        double acc[TR_CG];
+#pragma unroll
+        for (int u = 0; u < TR_CG; ++u) acc[u] = 0.0;
+        for (int p = 0; p < ro; ++p) {
+          const double r = Rm[j + (size_t)p * v.R];
+#pragma unroll
+          for (int u = 0; u < TR_CG; ++u) acc[u] += row[u][p] * r;
+        }
+#pragma unroll
+        for (int u = 0; u < TR_CG; ++u)
+          if (u < ni) blk[(i0 + u) + (size_t)j * v.R] = acc[u];
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  if (x == v.ns6) {
+    if (v.l < 3) return;
+    // V^dag_b := U^dag_b (both r_new x r_parent; zeros beyond the parent's rank)
+    for (int e = threadIdx.x; e < rn * v.Rp; e += blockDim.x) {
+      const int i = e % rn, j = e / rn;
+      v.vd(b)[i + (size_t)j * v.R] = v.ud(b)[i + (size_t)j * v.R];
+    }
+    return;
+  }
+  // a pending column-side P2P_qb (q not yet eliminated): M2P_qb = (P2L_bq)^T,
+  // P2L_bq written into LX(b, s) by the row side
+  const int s5 = x - v.ns6 - 1;
+  if (threadIdx.x == 0) sw = ws_block(v, b, s5, 1, c.col);
+  __syncthreads();
+  if (!sw.ok) return;
+  slot5_coords(bc, s5, v.d, q);
+  if (colour_of(q, v.d) < c.col) return;   // eliminated partner: part of the A_qb mirror
+  const int qb = morton_key(q, v.d, v.l);
+  const int mq = sw.rows;
+  double* dst = v.xy(qb, slot5(q, bc, v.d));
+  const double* src = v.lx(b, s5);
+  for (int e = threadIdx.x; e < mq * rn; e += blockDim.x) {
+    const int i = e % mq, j = e / mq;
+    dst[i + (size_t)j * v.M] = src[j + (size_t)i * v.R];
+  }
+}
+
 // column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
 // (the M2P block into y_b is zero before b is eliminated).
 // grid (ns5 * tpr, tiles over rn, cnt) with tpr row tiles per block.
@@ -1626,13 +1718,19 @@ static int factor_level(Handle& h, int l) {
     k_cmp_row_done<<<dim3(F.ns5 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     k_cmp_set_rank<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
-    dp.begin("col_transform");
-    k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
-    dp.end();
-    dp.begin("col_fill");
-    AIFMM_LAUNCH_PM(pm, k_cmp_col_fill, dim3(F.ns5 * tpc, rtl, cnt), v, c, tpc);
-    ++h.nlaunch;
-    dp.end();
+    if (h.sym) {
+      dp.begin("col_mirror");
+      k_cmp_col_mirror<<<dim3(F.ns6 + 1 + F.ns5, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+      dp.end();
+    } else {
+      dp.begin("col_transform");
+      k_cmp_col_transform<<<dim3(F.ns6 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
+      dp.end();
+      dp.begin("col_fill");
+      AIFMM_LAUNCH_PM(pm, k_cmp_col_fill, dim3(F.ns5 * tpc, rtl, cnt), v, c, tpc);
+      ++h.nlaunch;
+      dp.end();
+    }
     dp.begin("col_done");
     k_cmp_col_done<<<dim3(F.ns5 + 1, cnt), 256, 0, st>>>(v, c); ++h.nlaunch;
     dp.end();
