@@ -13,13 +13,24 @@ struct LuItem {
   int* ipiv;       // n row interchanges (LAPACK convention, 0-based)
   const double* colmax;  // n column maxima of the original matrix (singularity test)
   int n, ld;
+  // right-hand columns factored along with A (the augmented matrix [A | B]):
+  // the row interchanges, the panels' triangular solves and the trailing
+  // updates are applied to B too, which ends as L^-1 P B.  nb = 0: none.
+  double* b;       // column-major n x nb, leading dimension ldb
+  int ldb, nb;
 };
+
+// column c of the augmented matrix [A | B]
+__device__ inline double* lu_col(const LuItem& it, int c) {
+  return c < it.n ? it.a + (size_t)c * it.ld : it.b + (size_t)(c - it.n) * it.ldb;
+}
 
 constexpr int LU_NB = 32;
 
 // U12 = L11^-1 A12 for the columns right of the panel: one warp per column,
 // lane i holding row k0 + i, x_j broadcast with a shuffle (lane-dense FP64;
 // see k_lus_diag_w).  grid (column groups of 4, items), 128 threads
+// (columns of B included: grid columns cover n + nb)
 static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int k0) {
   __shared__ double L[LU_NB][LU_NB + 1];
   LuItem it = items[blockIdx.y];
@@ -35,8 +46,8 @@ static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int
   __syncthreads();
   const int lane = threadIdx.x & 31;
   int c = kend + blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (c >= n) return;
-  double* X = A + (size_t)c * ld + k0;
+  if (c >= n + it.nb) return;
+  double* X = lu_col(it, c) + k0;
   double x = lane < nb ? X[lane] : 0.0;
   for (int j = 0; j < nb; ++j) {
     double xj = __shfl_sync(0xffffffffu, x, j);
@@ -156,18 +167,29 @@ __device__ inline void tile_gemm(const double* A, int lda, const double* B, int 
   }
 }
 
-// A22 -= L21 U12 ; grid (coltiles, rowtiles, items); PM_FMA, PM_OZ8 or PM_F32
+// A22 -= L21 U12, and B2 -= L21 B1 for the right-hand columns; grid
+// (coltiles of A22 then of B, rowtiles, items); PM_FMA, PM_OZ8 or PM_F32
 template <int PM = PM_FMA>
 static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int k0) {
   LuItem it = items[blockIdx.z];
   int n = it.n;
   int kend = min(n, k0 + LU_NB);
-  int i0 = kend + blockIdx.y * 64, j0 = kend + blockIdx.x * 64;
-  if (k0 >= n || i0 >= n || j0 >= n) return;
+  int i0 = kend + blockIdx.y * 64;
+  if (k0 >= n || i0 >= n) return;
   double* A = it.a;
   const int ld = it.ld;
-  tile_gemm<PM>(A + i0 + (size_t)k0 * ld, ld, A + k0 + (size_t)j0 * ld, ld, A + i0 + (size_t)j0 * ld, ld,
-                n - i0, n - j0, kend - k0, -1.0);
+  const int ta = (n - kend + 63) / 64;          // column tiles of A22
+  if ((int)blockIdx.x < ta) {
+    const int j0 = kend + blockIdx.x * 64;
+    tile_gemm<PM>(A + i0 + (size_t)k0 * ld, ld, A + k0 + (size_t)j0 * ld, ld, A + i0 + (size_t)j0 * ld, ld,
+                  n - i0, n - j0, kend - k0, -1.0);
+    return;
+  }
+  const int jb = ((int)blockIdx.x - ta) * 64;
+  if (jb >= it.nb) return;
+  double* B = it.b;
+  tile_gemm<PM>(A + i0 + (size_t)k0 * ld, ld, B + k0 + (size_t)jb * it.ldb, it.ldb, B + i0 + (size_t)jb * it.ldb,
+                it.ldb, n - i0, it.nb - jb, kend - k0, -1.0);
 }
 
 // X := A^-1 X for an LU-factored A (ipiv interchanges, unit L, U), per item;
@@ -600,6 +622,9 @@ static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items,
     }
     __syncthreads();
     if (sing) {
+      // the interchanges of the columns not reached stay the identity, so
+      // the kernels that follow in this step read valid rows
+      for (int q = jj + threadIdx.x; q < nbw; q += blockDim.x) it.ipiv[k0 + q] = k0 + q;
       if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
       return;
     }
@@ -618,15 +643,16 @@ static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items,
 }
 
 // the panel's interchanges applied to every column outside the panel
-// (left: the L factor, right: the part still to be factored); grid (colchunks, items)
+// (left: the L factor, right: the part still to be factored, then B);
+// grid (colchunks over n + nb, items)
 static __global__ void __launch_bounds__(128) k_lu_laswp(const LuItem* items, int k0, int maxh) {
   LuItem it = items[blockIdx.y];
   const int n = it.n;
   if (k0 >= n || n - k0 > maxh) return;
   const int nbw = min(LU_NB, n - k0);
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n || (c >= k0 && c < k0 + nbw)) return;
-  double* col = it.a + (size_t)c * it.ld;
+  if (c >= n + it.nb || (c >= k0 && c < k0 + nbw)) return;
+  double* col = lu_col(it, c);
   for (int jj = 0; jj < nbw; ++jj) {
     int p = it.ipiv[k0 + jj];
     if (p != k0 + jj) {
@@ -641,7 +667,8 @@ static __global__ void __launch_bounds__(128) k_lu_laswp(const LuItem* items, in
 static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items, int k0, int maxh, int* err) {
   LuItem it = items[blockIdx.x];
   if (k0 >= it.n || it.n - k0 <= maxh) return;
-  // the panel algorithm of k_lu_panel_sm in global memory, full-row interchanges
+  // the panel algorithm of k_lu_panel_sm in global memory, full-row
+  // interchanges (through the columns of B too)
   __shared__ double shv[32];
   __shared__ int shi[32];
   int n = it.n;
@@ -662,15 +689,17 @@ static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items
     int p = best.i;
     double cm = it.colmax ? it.colmax[j] : 0.0;
     if (!(best.v > 1e-14 * cm) || !(best.v >= LU_PIV_MIN)) {
+      for (int q = j + threadIdx.x; q < kend; q += blockDim.x) it.ipiv[q] = q;
       if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
       return;
     }
     if (threadIdx.x == 0) it.ipiv[j] = p;
     if (p != j)
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double t = A[j + (size_t)c * ld];
-        A[j + (size_t)c * ld] = A[p + (size_t)c * ld];
-        A[p + (size_t)c * ld] = t;
+      for (int c = threadIdx.x; c < n + it.nb; c += blockDim.x) {
+        double* col = lu_col(it, c);
+        double t = col[j];
+        col[j] = col[p];
+        col[p] = t;
       }
     __syncthreads();
     const double rpiv = 1.0 / A[j + (size_t)j * ld];

@@ -1152,6 +1152,11 @@ __global__ void k_coupled(LV v, Elim e) {
   it.colmax = e.colmax + (size_t)t * v.P;
   it.n = mb + rb;
   it.ld = v.P;
+  // the coupled columns B (k_z_build) are factored along: the LU leaves
+  // L^-1 P B in Z, and only the upper triangular solve remains
+  it.b = e.Z + (size_t)t * v.P * e.ncmax;
+  it.ldb = v.P;
+  it.nb = co;
   e.lu[t] = it;
   SolveItem si;
   si.a = v.lu(b);
@@ -1195,9 +1200,8 @@ __global__ void k_piv_build(LV v, Elim e) {
 }
 
 // B = A[pivot rows, coupled columns]: [c_C; 0] for x_q / y_q, [0; -I] for y_b,
-// stored with the pivot LU's row interchanges already applied (row i of Z
-// holds row pp[i] of B)
-// grid (MAXC, cnt, ZB_SLICES): slice z takes the columns j = z, z + ZB_SLICES, ...
+// in the pivot block's row order (the LU of [Piv | B] interchanges its rows)
+// grid (coupled entities, cnt, ZB_SLICES): slice z takes the columns j = z, z + ZB_SLICES, ...
 constexpr int ZB_SLICES = 4;
 __global__ void k_z_build(LV v, Elim e) {
   int t = blockIdx.y, ci = blockIdx.x;
@@ -1208,13 +1212,12 @@ __global__ void k_z_build(LV v, Elim e) {
   const int m = v.m[b], r = v.r[b], n = m + r, P = v.P;
   Coupled C = e.cols[(size_t)t * MAXC + ci];
   double* Z = e.Z + (size_t)t * P * e.ncmax + (size_t)C.off * P;
-  const int* pr = v.pp(b);
   const int z = blockIdx.z;
   const int nj = C.size > z ? (C.size - z + ZB_SLICES - 1) / ZB_SLICES : 0;
   if (C.type == 2) {
     for (int x = threadIdx.x; x < n * nj; x += blockDim.x) {
       int i = x % n, j = z + ZB_SLICES * (x / n);
-      Z[i + (size_t)j * P] = (pr[i] - m == j) ? -1.0 : 0.0;
+      Z[i + (size_t)j * P] = (i - m == j) ? -1.0 : 0.0;
     }
     return;
   }
@@ -1223,8 +1226,7 @@ __global__ void k_z_build(LV v, Elim e) {
   const double* src = C.type == 0 ? v.xx(b, s) : v.xy(b, s);
   for (int x = threadIdx.x; x < n * nj; x += blockDim.x) {
     int i = x % n, j = z + ZB_SLICES * (x / n);
-    int r = pr[i];
-    Z[i + (size_t)j * P] = r < m ? src[r + (size_t)j * v.M] : 0.0;
+    Z[i + (size_t)j * P] = i < m ? src[i + (size_t)j * v.M] : 0.0;
   }
 }
 
@@ -1756,41 +1758,46 @@ static int factor_level(Handle& h, int l) {
     gt = new GroupTimer(h, Handle::G_PIVLU);
     dp.begin("piv_build");
     k_piv_build<<<dim3(cnt, PB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
+    k_z_build<<<dim3(ipow(3, d) + 1, cnt, ZB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
     dp.end();
     k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P); ++h.nlaunch;
     dp.begin("lu");
     {
+      // LU with partial pivoting of [Piv | B] (B = the coupled columns,
+      // k_z_build): the interchanges, the panels' unit-lower solves and the
+      // trailing updates also reach B, which ends as L^-1 P B (the forward
+      // half of Z = Piv^-1 B), every trailing update a tile GEMM on the
+      // tensor cores with 8 digits and the balanced contraction (a column of
+      // B mixes entries of very different sizes; see below); fma_gemm: FP64
+      // FMAs
       const int maxh = h.panel_rows;
+      const int ctot = F.P + e.ncmax;
+      const int tiles = (F.P + 63) / 64, ctiles = tiles + (e.ncmax + 63) / 64;
       for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
         const int hh = std::min(F.P - k0, maxh);
         k_lu_panel_sm<<<cnt, 256, sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
         if (F.P - k0 > maxh) {
           k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
         }
-        k_lu_laswp<<<dim3((F.P + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
-        k_lu_trsm<<<dim3((F.P + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
-        int tiles = (F.P + 63) / 64;
+        k_lu_laswp<<<dim3((ctot + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
+        k_lu_trsm<<<dim3((ctot + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
         if (pm == PM_F32)
-          k_lu_gemm<PM_F32><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+          k_lu_gemm<PM_F32><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         else if (pm == PM_OZ)
-          k_lu_gemm<PM_OZ8><<<dim3(tiles, tiles, cnt), 256, OZ_SMEM8, st>>>(e.lu, k0);
+          k_lu_gemm<PM_OZ8><<<dim3(ctiles, tiles, cnt), 256, OZ_SMEM8, st>>>(e.lu, k0);
         else
-          k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+          k_lu_gemm<PM_FMA><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         ++h.nlaunch;
       }
     }
     k_piv_perm<<<(cnt + 127) / 128, 128, 0, st>>>(v, col, cnt); ++h.nlaunch;
     dp.end();
     delete gt;
-    // ---- Z = Piv^-1 B and the Schur update
+    // ---- Z = U^-1 (L^-1 P B) and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
-    dp.begin("z_build");
-    k_z_build<<<dim3(MAXC, cnt, ZB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
-    dp.end();
     {
-      // blocked LU solve of Z (interchanges applied by k_z_build): unit-lower
-      // blocks downwards, upper blocks upwards, each trailing update a tiled
-      // GEMM on the tensor cores with 8 digits (56-bit slices) and the
+      // blocked upper triangular solve of Z, upwards, each trailing update a
+      // tiled GEMM on the tensor cores with 8 digits (56-bit slices) and the
       // balanced contraction.  A column of Z mixes the x part, of size
       // ~1/A_ii, with the z part, orders of magnitude larger, inside one
       // 64-row chunk: with 7 digits and one exponent per column the small
@@ -1802,24 +1809,6 @@ static int factor_level(Handle& h, int l) {
       const int ctiles = (e.ncmax + 63) / 64;
       const int wstr = (e.ncmax + 3) / 4, cstr = (e.ncmax + 127) / 128;
       const bool wdiag = lus_warp_diag(cnt, e.ncmax);
-      for (int k0 = 0; k0 < F.P; k0 += TB) {
-        if (wdiag) {
-          k_lus_diag_w<1><<<dim3(wstr, cnt), 128, 0, st>>>(e.sv, k0);
-        } else {
-          k_lus_diag<1><<<dim3(cstr, cnt), 128, 0, st>>>(e.sv, k0);
-        }
-        ++h.nlaunch;
-        if (k0 + TB < F.P) {
-          const dim3 g(ctiles, (F.P - k0 - TB + 63) / 64, cnt);
-          if (pm == PM_F32)
-            k_lus_update<1, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
-          else if (pm == PM_OZ)
-            k_lus_update<1, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(e.sv, k0);
-          else
-            k_lus_update<1, PM_FMA><<<g, 256, 0, st>>>(e.sv, k0);
-          ++h.nlaunch;
-        }
-      }
       for (int k0 = ((F.P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
         if (wdiag) {
           k_lus_diag_w<0><<<dim3(wstr, cnt), 128, 0, st>>>(e.sv, k0);
@@ -1907,7 +1896,8 @@ static double level_flops(Handle& h, int l) {
       cols += sz;
       ssq += sz * sz;
     }
-    double flu = 2.0 / 3.0 * n * n * n, fz = 2.0 * n * n * cols, fs = 2.0 * (rows - r) * m * cols;
+    // the forward half of Z = Piv^-1 B runs inside the LU of [Piv | B]
+    double flu = 2.0 / 3.0 * n * n * n + n * n * cols, fz = n * n * cols, fs = 2.0 * (rows - r) * m * cols;
     if (h.sym) {
       // blocks (i, j) with i <= j only: neighbour pairs and the y_b column
       double sn = rows - r;
@@ -1994,6 +1984,9 @@ int run_factor(Handle& h) {
   hi.colmax = cm;
   hi.n = h.ntop;
   hi.ld = h.ntop;
+  hi.b = nullptr;
+  hi.ldb = 0;
+  hi.nb = 0;
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(it, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
   k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
