@@ -72,8 +72,11 @@ typedef enum { AIFMM_K_LOG2D = 0, AIFMM_K_INVR3D = 1, AIFMM_K_INVR2D = 2, AIFMM_
 typedef struct {
   int kind;        /* aifmm_kernel_kind */
   int dim;         /* 2 or 3 */
-  double diag;     /* A_ii */
+  double diag;     /* A_ii; NaN: kernel(0) + nugget (GAUSS only: 1 + nugget;
+                      INVALID for the kernels that are infinite at r = 0) */
   double length;   /* Gaussian length scale (GAUSS only) */
+  double nugget;   /* added to kernel(0) when diag is NaN (a Gaussian-process
+                      noise variance); finite; ignored otherwise */
 } aifmm_kernel;
 
 typedef struct {
@@ -107,7 +110,17 @@ typedef struct {
                       QR that fixes the compression ranks, the panels and the
                       triangular blocks stay FP64.  A factorisation for preconditioning
                       aifmm_gmres (Sec. 4, AIFMM as a preconditioner); aifmm_solve with
-                      it has a relative error of about 1e-6 */
+                      it has a relative error of about 1e-6.  2: the same products
+                      on the tensor cores in TF32 (10-bit mantissa operands) with FP32
+                      accumulation (mma.sync m16n8k8 tiles; FP32 FMAs for products
+                      of at most 8 columns); relative error of a solve about 1e-3,
+                      a preconditioner only; its compress threshold (factor_tol)
+                      must sit above TF32 rounding, ~1e-3 */
+  double eta;      /* admissibility parameter of Sec. 2.2 (max diameter <= eta x
+                      distance): 0 (default) or any eta >= sqrt(dim), which all give
+                      the same lists for the boxes of a uniform tree (neighbours =
+                      touching boxes); eta < sqrt(dim) is INVALID (it would need a
+                      near field wider than the touching boxes) */
 } aifmm_options;
 
 /* Per-handle statistics (aifmm_stats). Times are CUDA-event milliseconds of

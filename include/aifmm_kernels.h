@@ -48,6 +48,16 @@ int aifmm_dgemm_tc8(const double* A, int64_t lda, const double* B, int64_t ldb, 
 int aifmm_dgemm_tc05(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                      int k, double alpha, void* stream);
 
+/* C += alpha * op(A) * B on the tensor cores in TF32 with FP32 accumulation
+ * (the tile of the factorisation's precision = 2 mode): op(A) = A (m x k,
+ * trans_a = 0) or A^T (A k x m, trans_a != 0); operands rounded FP64 ->
+ * FP32 -> TF32 (10-bit mantissa, round to nearest), products summed in FP32,
+ * added to C in FP64; error about 2^-10 |op(A)| |B|.  DEVICE pointers,
+ * column-major, lda >= (trans_a ? k : m), ldb >= k, ldc >= m (each < 2^31);
+ * the call synchronises `stream`.  Returns 0, 1 (invalid argument) or 6. */
+int aifmm_gemm_tf32(int trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                    int m, int n, int k, double alpha, void* stream);
+
 /* Measured FMA throughput of the current device, for roofline peaks: every
  * thread of 8 x (SM count) CTAs of 256 threads runs 8 independent FMA chains
  * of 16,384 steps; *tflops receives 2 x FMAs / time in TFLOP/s, the best of

@@ -34,13 +34,14 @@ class AifmmError(RuntimeError):
 
 
 class Kernel(C.Structure):
-    _fields_ = [("kind", C.c_int), ("dim", C.c_int), ("diag", C.c_double), ("length", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("dim", C.c_int), ("diag", C.c_double), ("length", C.c_double),
+                ("nugget", C.c_double)]
 
 
 class Options(C.Structure):
     _fields_ = [("order", C.c_int), ("depth", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
                 ("no_symmetry", C.c_int), ("factor_tol", C.c_double), ("fma_gemm", C.c_int),
-                ("tcgen05", C.c_int), ("precision", C.c_int)]
+                ("tcgen05", C.c_int), ("precision", C.c_int), ("eta", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -79,6 +80,8 @@ def lib():
         L.aifmm_dgemm_tc05.restype = C.c_int
         L.aifmm_dgemm_tc8.argtypes = [vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
         L.aifmm_dgemm_tc8.restype = C.c_int
+        L.aifmm_gemm_tf32.argtypes = [cint, vp, i64, vp, i64, vp, i64, cint, cint, cint, dbl, vp]
+        L.aifmm_gemm_tf32.restype = C.c_int
         L.aifmm_fma_rate.argtypes = [cint, vp, C.POINTER(dbl)]
         L.aifmm_fma_rate.restype = C.c_int
         L.aifmm_tree_perm.argtypes = [vp, vp, vp]
@@ -160,7 +163,7 @@ class Handle:
 def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, length: float = 1.0,
                 depth: int = 0, stream=None, profile: bool = False, symmetric: bool = True,
                 factor_tol: float = 0.0, fma_gemm: bool = False, tcgen05: bool = False,
-                fp32: bool = False) -> Handle:
+                fp32: bool = False, nugget: float = 0.0, eta: float = 0.0, tf32: bool = False) -> Handle:
     """Build tree, lists, NNCA operators and the extended system (C: aifmm_build).
 
     ``symmetric=False`` selects the general elimination (rows and columns
@@ -170,7 +173,8 @@ def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, le
     the tensor cores;
     ``tcgen05`` issues them on tcgen05.mma instead of warp MMAs; ``fp32``
     makes the factorisation's tile products FP32 (a preconditioner for
-    aifmm_gmres)."""
+    aifmm_gmres), ``tf32`` TF32 tensor-core products (the same use).  ``diag`` = NaN makes A_ii = kernel(0) + ``nugget``
+    (Gaussian only); ``eta`` is the admissibility parameter (0 or >= sqrt(dim))."""
     if isinstance(points, np.ndarray):
         points = np.ascontiguousarray(points, dtype=np.float64)
     else:
@@ -178,9 +182,10 @@ def aifmm_build(points, kernel: int, diag: float, tol: float, leaf_size: int, le
     if points.ndim != 2:
         raise ValueError("points must be N x dim")
     n, dim = points.shape
-    k = Kernel(kernel, dim, float(diag), float(length))
+    k = Kernel(kernel, dim, float(diag), float(length), float(nugget))
     o = Options(0, int(depth), C.c_void_p(stream) if stream else None, int(bool(profile)), int(not symmetric),
-                float(factor_tol), int(bool(fma_gemm)), int(bool(tcgen05)), int(bool(fp32)))
+                float(factor_tol), int(bool(fma_gemm)), int(bool(tcgen05)), 2 if tf32 else int(bool(fp32)),
+                float(eta))
     out = C.c_void_p()
     _ready(None, points)
     p, keep = _ptr(points)
@@ -308,6 +313,23 @@ def aifmm_dgemm_tc(A, B, C_, alpha: float = 1.0, stream=None, tcgen05: bool = Fa
                               C.c_void_p(stream) if stream else None)
     if st != 0:
         raise AifmmError(st, "aifmm_dgemm_tc failed")
+
+
+def aifmm_gemm_tf32(A, B, C_, alpha: float = 1.0, trans_a: bool = False, stream=None) -> None:
+    """C_ += alpha op(A) B on the TF32 tensor cores (C: aifmm_gemm_tf32); CUDA
+    float64 column-major tensors; op(A) = A^T with ``trans_a``."""
+    import torch
+    m, n = C_.shape
+    k = B.shape[0]
+    assert A.dtype == B.dtype == C_.dtype == torch.float64
+    def ld(t):
+        assert t.is_cuda and (t.stride(0) == 1 or t.shape[0] == 1), "column-major CUDA tensors"
+        return max(1, t.shape[0], t.stride(1) if t.shape[1] > 1 else 1)
+    st = lib().aifmm_gemm_tf32(int(bool(trans_a)), C.c_void_p(A.data_ptr()), ld(A), C.c_void_p(B.data_ptr()), ld(B),
+                               C.c_void_p(C_.data_ptr()), ld(C_), m, n, k, float(alpha),
+                               C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise AifmmError(st, "aifmm_gemm_tf32 failed")
 
 
 def aifmm_fma_rate(fp32: bool = False, stream=None) -> float:

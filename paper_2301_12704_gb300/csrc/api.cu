@@ -235,12 +235,31 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   if (out) *out = nullptr;
   g_build_err.clear();
   if (!points || !k || !out || n < 1 || n > (int64_t)1 << 30 || (k->dim != 2 && k->dim != 3) ||
-      !(tol >= 0.0) || leaf_size < 1 || k->kind < 0 || k->kind > 3 || !std::isfinite(k->diag) ||
-      (k->kind == AIFMM_K_GAUSS && !(k->length > 0.0)) || (opt && opt->order != 0) ||
-      (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12)) ||
+      !(tol >= 0.0) || leaf_size < 1 || k->kind < 0 || k->kind > 3 || std::isinf(k->diag) ||
+      !std::isfinite(k->nugget) || (k->kind == AIFMM_K_GAUSS && !(k->length > 0.0)) ||
+      (opt && opt->order != 0) || (opt && opt->depth != 0 && (opt->depth < 2 || opt->depth > 12)) ||
       (opt && !(opt->factor_tol >= 0.0 && std::isfinite(opt->factor_tol))) ||
-      (opt && (opt->precision < 0 || opt->precision > 1))) {
+      (opt && (opt->precision < 0 || opt->precision > 2)) || (opt && !(opt->eta >= 0.0))) {
     g_build_err = "invalid argument";
+    return AIFMM_ERR_INVALID;
+  }
+  // A_ii: diag, or kernel(0) + nugget when diag is NaN (finite only for the
+  // Gaussian, whose value at r = 0 is 1)
+  double diag = k->diag;
+  if (std::isnan(diag)) {
+    if (k->kind != AIFMM_K_GAUSS) {
+      g_build_err = "invalid argument: diag = NaN asks for kernel(0) + nugget, infinite for this kernel";
+      return AIFMM_ERR_INVALID;
+    }
+    diag = 1.0 + k->nugget;
+  }
+  // admissibility max(diam X, diam Y) <= eta dist(X, Y) (Sec. 2.2): for
+  // boxes of one level, touching boxes are never admissible and boxes one
+  // box apart are admissible exactly when eta >= sqrt(d), so every
+  // eta >= sqrt(d) gives the lists built here; a smaller eta needs a wider
+  // near field, which the library does not build
+  if (opt && opt->eta != 0.0 && opt->eta < std::sqrt((double)k->dim) * (1.0 - 1e-12)) {
+    g_build_err = "invalid argument: eta below sqrt(dim) needs a near field wider than the neighbouring boxes";
     return AIFMM_ERR_INVALID;
   }
   aifmm_ctx* c = new aifmm_ctx();
@@ -253,13 +272,14 @@ aifmm_status aifmm_build(const double* points, int64_t n, const aifmm_kernel* k,
   h.leaf = leaf_size;
   h.kp.kind = k->kind;
   h.kp.dim = k->dim;
-  h.kp.diag = k->diag;
+  h.kp.diag = diag;
   h.kp.inv_len2 = k->kind == AIFMM_K_GAUSS ? 1.0 / (k->length * k->length) : 0.0;
   h.profile = opt && opt->profile;
   h.sym = !(opt && opt->no_symmetry);
   h.fma_gemm = opt && opt->fma_gemm;
   h.tc05 = opt && opt->tcgen05;
   h.fp32 = opt && opt->precision == 1;
+  h.tf32 = opt && opt->precision == 2;
   if (opt && opt->stream) {
     h.stream = (cudaStream_t)opt->stream;
   } else {

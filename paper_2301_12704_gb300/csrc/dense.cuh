@@ -139,6 +139,102 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
     }
 }
 
+// 64x64 tile on the tensor cores in TF32 with FP32 accumulation (the
+// preconditioner's low-precision products, aifmm_options.precision = 2):
+// C[0..mr, 0..nc] += alpha * op(A) B, op(A) = A (column-major, lda) or, with
+// TA, A^T for A column-major K x mr.  K in chunks of 32: the chunk's
+// operands are rounded FP64 -> FP32 -> TF32 (round to nearest, ties away)
+// into shared memory; 8 warps, each a 32 x 16 sub-tile of 2 x 2
+// mma.sync m16n8k8 tf32 products per 8 of K, FP32 accumulators; the
+// result is added to C in FP64.  Products of TF32 values are exact in the
+// FP32 accumulator, so the error is the operands' rounding (2^-11 relative)
+// plus the FP32 sums.  256 threads; 18 KB of static shared memory.
+constexpr int TF_KC = 32;
+constexpr int TF_LD = TF_KC + 4;            // padded rows: conflict-free fragment loads
+
+__device__ inline uint32_t tf32_bits(double x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)x));
+  return u;
+}
+
+__device__ inline void tf32_mma(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TA = false>
+__device__ inline void tile_gemm_64_tf32(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                         int mr, int nc, int K, double alpha) {
+  __shared__ uint32_t As[64][TF_LD];   // (row of op(A), k)
+  __shared__ uint32_t Bs[64][TF_LD];   // (column of B, k)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int r0 = 32 * (w & 1), c0 = 16 * (w >> 1);
+  float acc[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += TF_KC) {
+    const int kc = min(TF_KC, K - k0);
+    for (int e = threadIdx.x; e < 64 * TF_KC; e += blockDim.x) {
+      int i, k;
+      if (TA) {
+        k = e & (TF_KC - 1);
+        i = e / TF_KC;
+      } else {
+        i = e & 63;
+        k = e >> 6;
+      }
+      double a = 0.0;
+      if (i < mr && k < kc) a = TA ? A[(k0 + k) + (size_t)i * lda] : A[i + (size_t)(k0 + k) * lda];
+      As[i][k] = tf32_bits(a);
+      const int kb = e & (TF_KC - 1), j = e / TF_KC;
+      const double bv = (j < nc && kb < kc) ? B[(k0 + kb) + (size_t)j * ldb] : 0.0;
+      Bs[j][kb] = tf32_bits(bv);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k8 = 0; k8 < TF_KC; k8 += 8) {
+      uint32_t af[2][4], bf[2][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r = r0 + 16 * mi + g;
+        af[mi][0] = As[r][k8 + tq];
+        af[mi][1] = As[r + 8][k8 + tq];
+        af[mi][2] = As[r][k8 + tq + 4];
+        af[mi][3] = As[r + 8][k8 + tq + 4];
+      }
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) {
+        const int c = c0 + 8 * ni + g;
+        bf[ni][0] = Bs[c][k8 + tq];
+        bf[ni][1] = Bs[c][k8 + tq + 4];
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) tf32_mma(acc[mi][ni], af[mi], bf[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = r0 + 16 * mi + g + 8 * (q >> 1), j = c0 + 8 * ni + 2 * tq + (q & 1);
+        if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * (double)acc[mi][ni][q];
+      }
+}
+
 // Product modes of the tile kernels: PM_FMA FP64 FMAs; PM_OZ FP64 precision
 // on the BF16 warp MMAs (ozaki.cuh, for more than THIN_NC columns; kernels
 // instantiated with it are launched with OZ_SMEM bytes of dynamic shared
@@ -148,7 +244,10 @@ __device__ inline void tile_gemm_64(const double* A, int lda, const double* B, i
 // PM_OZ8: the warp-MMA tile with 8 digits (56-bit slices) and the balanced
 // contraction (the Z = Piv^-1 B solve and the pivot LU's trailing updates,
 // whose operands mix entries of very different sizes; oz_smem(OZ_S8) bytes).
-enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3, PM_OZ8 = 4 };
+// PM_TF32: TF32 tensor-core products with FP32 sums (tile_gemm_64_tf32) for
+// more than THIN_NC columns, FP32 FMAs for fewer (the preconditioner's
+// low-precision mode, aifmm_options.precision = 2).
+enum { PM_FMA = 0, PM_OZ = 1, PM_TC05 = 2, PM_F32 = 3, PM_OZ8 = 4, PM_TF32 = 5 };
 
 // C += alpha A B, 64 x 64 tile (A column-major lda, B column-major ldb)
 template <int PM>
@@ -160,7 +259,9 @@ __device__ inline void tile_gemm(const double* A, int lda, const double* B, int 
   } else if (PM == PM_OZ8 && nc > THIN_NC) {
     extern __shared__ __align__(16) unsigned char oz_dyn[];
     tile_gemm_64_oz<false, true, OZ_S8>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, oz_dyn);
-  } else if (PM == PM_F32) {
+  } else if (PM == PM_TF32 && nc > THIN_NC) {
+    tile_gemm_64_tf32<false>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
+  } else if (PM == PM_F32 || PM == PM_TF32) {
     tile_gemm_64<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
   } else {
     tile_gemm_64(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
@@ -553,7 +654,9 @@ __device__ inline void tile_gemm_tn(const double* A, int lda, const double* B, i
   if (PM == PM_OZ && nc > THIN_NC) {
     extern __shared__ __align__(16) unsigned char oz_dyn[];
     tile_gemm_64_oz<true>(A, lda, B, ldb, C, ldc, min(64, mr), min(64, nc), K, alpha, oz_dyn);
-  } else if (PM == PM_F32) {
+  } else if (PM == PM_TF32 && nc > THIN_NC) {
+    tile_gemm_64_tf32<true>(A, lda, B, ldb, C, ldc, min(64, mr), min(64, nc), K, alpha);
+  } else if (PM == PM_F32 || PM == PM_TF32) {
     tile_gemm_64_tn<float>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);
   } else {
     tile_gemm_64_tn(A, lda, B, ldb, C, ldc, mr, nc, K, alpha);

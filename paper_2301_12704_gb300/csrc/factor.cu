@@ -1323,6 +1323,8 @@ __device__ __forceinline__ void schur_tile(const LV& v, const Elim& e, const Sch
     tile_gemm_64_oz(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0, ozs);
   } else if (PM == PM_F32) {
     tile_gemm_64<float>(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
+  } else if (PM == PM_TF32) {
+    tile_gemm<PM_TF32>(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   } else {
     tile_gemm_64(A + i0, lda, Z, P, T, ldt, mr, nc, m, -1.0);
   }
@@ -1405,14 +1407,18 @@ __global__ void k_xoff(int nb, int d, const int* __restrict__ r, int* __restrict
       KERN<PM_OZ><<<(grid), 256, OZ_SMEM, st>>>(__VA_ARGS__);                  \
     else if ((pm) == PM_F32)                                                   \
       KERN<PM_F32><<<(grid), 256, 0, st>>>(__VA_ARGS__);                       \
+    else if ((pm) == PM_TF32)                                                  \
+      KERN<PM_TF32><<<(grid), 256, 0, st>>>(__VA_ARGS__);                      \
     else                                                                       \
       KERN<PM_FMA><<<(grid), 256, 0, st>>>(__VA_ARGS__);                       \
   } while (0)
 
 // product mode of the compress fills and projections, the Schur update
-// (unless tcgen05 is chosen there) and, with PM_F32, of the Z solve and the
+// (unless tcgen05 is chosen there) and, with PM_F32 or PM_TF32, of the Z solve and the
 // pivot LU's trailing updates
-static int product_mode(const Handle& h) { return h.fp32 ? PM_F32 : h.fma_gemm ? PM_FMA : PM_OZ; }
+static int product_mode(const Handle& h) {
+  return h.tf32 ? PM_TF32 : h.fp32 ? PM_F32 : h.fma_gemm ? PM_FMA : PM_OZ;
+}
 
 // CTAs of the persistent Schur kernel that fit on one SM at once, per
 // product mode (queried once per handle)
@@ -1424,6 +1430,7 @@ static int schur_ctas_per_sm(Handle& h, int pm) {
     int nb = 0;
     cudaError_t e = pm == PM_OZ   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_OZ>, 256, OZ_SMEM)
                     : pm == PM_F32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_F32>, 256, 0)
+                    : pm == PM_TF32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_TF32>, 256, 0)
                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_schur<PM_FMA>, 256, 0);
     if (e != cudaSuccess || nb < 1) {
       cudaGetLastError();
@@ -1783,6 +1790,8 @@ static int factor_level(Handle& h, int l) {
         k_lu_trsm<<<dim3((ctot + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
         if (pm == PM_F32)
           k_lu_gemm<PM_F32><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
+        else if (pm == PM_TF32)
+          k_lu_gemm<PM_TF32><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         else if (pm == PM_OZ)
           k_lu_gemm<PM_OZ8><<<dim3(ctiles, tiles, cnt), 256, OZ_SMEM8, st>>>(e.lu, k0);
         else
@@ -1820,6 +1829,8 @@ static int factor_level(Handle& h, int l) {
           const dim3 g(ctiles, (k0 + 63) / 64, cnt);
           if (pm == PM_F32)
             k_lus_update<0, PM_F32><<<g, 256, 0, st>>>(e.sv, k0);
+          else if (pm == PM_TF32)
+            k_lus_update<0, PM_TF32><<<g, 256, 0, st>>>(e.sv, k0);
           else if (pm == PM_OZ)
             k_lus_update<0, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(e.sv, k0);
           else

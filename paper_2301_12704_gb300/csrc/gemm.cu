@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "../../include/aifmm_kernels.h"
+#include "dense.cuh"
 #include "ozaki.cuh"
 #include "tc05.cuh"
 
@@ -180,4 +181,38 @@ extern "C" int aifmm_fma_rate(int fp32, void* stream, double* tflops) {
   if (!tflops) return 1;
   *tflops = 0.0;
   return fp32 ? aifmm::fma_rate<float>(stream, tflops) : aifmm::fma_rate<double>(stream, tflops);
+}
+
+// ---------------------------------------------------------------------------
+// The TF32 tensor-core tile of the preconditioner mode, on its own.
+namespace aifmm {
+namespace {
+
+template <bool TA>
+__global__ void __launch_bounds__(256) k_gemm_tf32(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                                   double* C, int64_t ldc, int m, int n, int k, double alpha) {
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const double* Ab = TA ? A + (size_t)i0 * lda : A + i0;
+  tile_gemm_64_tf32<TA>(Ab, (int)lda, B + (size_t)j0 * ldb, (int)ldb, C + i0 + (size_t)j0 * ldc, (int)ldc,
+                        min(64, m - i0), min(64, n - j0), k, alpha);
+}
+
+}  // namespace
+}  // namespace aifmm
+
+extern "C" int aifmm_gemm_tf32(int trans_a, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                               int64_t ldc, int m, int n, int k, double alpha, void* stream) {
+  if (!A || !B || !C || m < 0 || n < 0 || k < 0 || lda < (trans_a ? k : m) || ldb < k || ldc < m ||
+      lda > INT32_MAX || ldb > INT32_MAX || ldc > INT32_MAX)
+    return 1;
+  if (m == 0 || n == 0) return 0;
+  dim3 grid((n + 63) / 64, (m + 63) / 64);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (trans_a)
+    aifmm::k_gemm_tf32<true><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, m, n, k, alpha);
+  else
+    aifmm::k_gemm_tf32<false><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, m, n, k, alpha);
+  if (cudaGetLastError() != cudaSuccess) return 6;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 6;
+  return 0;
 }

@@ -103,6 +103,7 @@ struct Handle {
   bool fma_gemm = false;   // Schur tiles on FP64 FMAs instead of the tensor-core emulation
   bool tc05 = false;       // Schur tiles on tcgen05 (TMEM accumulators) instead of the warp MMAs
   bool fp32 = false;       // FP32 products in the factorisation (preconditioner)
+  bool tf32 = false;       // TF32 tensor-core products in the factorisation (preconditioner)
   // kernel groups of the factorisation timed in profile mode; G_QRCP and
   // G_SCHUR are single kernels (k_cmp_qrcp, k_schur)
   enum { G_COMPRESS = 0, G_PIVLU = 1, G_ZSOLVE = 2, G_SCHUR = 3, G_QRCP = 4, G_NG = 5 };

@@ -45,3 +45,26 @@ def test_invalid_arguments_rejected_without_gpu_work():
     assert lib.aifmm_solve(None, None, None, 1, 1) == 1
     assert lib.aifmm_levels(None) == 0
     lib.aifmm_destroy(None)
+
+
+def test_nugget_and_eta_arguments_checked_before_gpu_work():
+    """diag = NaN asks for A_ii = kernel(0) + nugget, which is infinite for
+    the log and 1/r kernels; an admissibility parameter eta below sqrt(dim)
+    would need a wider near field than the touching boxes: both are refused
+    before any device work (so without a GPU)."""
+    import ctypes as C
+    import numpy as np
+    lib = A.lib()
+    pts = np.random.default_rng(0).uniform(-1, 1, (64, 2))
+    out = C.c_void_p()
+    k = A.Kernel(A.LOG2D, 2, float("nan"), 1.0, 0.1)
+    st = lib.aifmm_build(C.c_void_p(pts.ctypes.data), 64, C.byref(k), 1e-8, 16, None, C.byref(out))
+    assert st == 1 and out.value is None and b"kernel(0)" in lib.aifmm_last_error(None)
+    k = A.Kernel(A.LOG2D, 2, 64.0, 1.0, 0.0)
+    o = A.Options()
+    o.eta = 1.0                                   # below sqrt(2)
+    st = lib.aifmm_build(C.c_void_p(pts.ctypes.data), 64, C.byref(k), 1e-8, 16, C.byref(o), C.byref(out))
+    assert st == 1 and b"eta" in lib.aifmm_last_error(None)
+    k = A.Kernel(A.GAUSS, 2, float("inf"), 0.1, 0.0)
+    st = lib.aifmm_build(C.c_void_p(pts.ctypes.data), 64, C.byref(k), 1e-8, 16, None, C.byref(out))
+    assert st == 1

@@ -89,3 +89,48 @@ def test_fp32_option_checked(A):
     p = np.ascontiguousarray(pts)
     st = lib.aifmm_build(C.c_void_p(p.ctypes.data), len(p), C.byref(k), w.tol, w.leaf, C.byref(o), C.byref(out))
     assert st == 1 and out.value is None
+
+
+@pytest.mark.parametrize("trans_a", [False, True], ids=["AB", "AtB"])
+def test_tf32_tile_within_its_rounding(A, trans_a):
+    """The TF32 tile (aifmm_options.precision = 2) against the FP64 product:
+    each operand rounds to 10 mantissa bits (2^-11 relative), the products
+    are exact in FP32 and the FP32 sums add ~K 2^-24, so every entry is
+    within 2^-9 |op(A)| |B| of the exact one; ragged sizes over several
+    tiles and K chunks."""
+    import torch
+    g = torch.Generator().manual_seed(5)
+    m, n, k = 150, 133, 101
+    Aop = torch.randn(m, k, generator=g, dtype=torch.float64)
+    Bm = torch.randn(k, n, generator=g, dtype=torch.float64)
+    C0 = torch.randn(m, n, generator=g, dtype=torch.float64)
+    dev = torch.device("cuda", 0)
+    Ad = (Aop.t() if trans_a else Aop).to(dev).t().contiguous().t()   # column-major
+    Bd = Bm.to(dev).t().contiguous().t()
+    Cd = C0.to(dev).t().contiguous().t()
+    A.aifmm_gemm_tf32(Ad, Bd, Cd, alpha=-0.5, trans_a=trans_a)
+    exact = C0 - 0.5 * Aop @ Bm
+    bound = 2.0 ** -9 * 0.5 * (Aop.abs() @ Bm.abs())
+    err = (Cd.cpu() - exact).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
+    assert float((err / bound).max()) > 1e-3            # the rounding is visible: not an FP64 product
+
+
+@pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
+def test_tf32_factor_preconditions_fp64_gmres(A, w):
+    pts, b = W.points_and_rhs(w)
+    b = b[:, 0]
+    # TF32 rounding of the products sits near 1e-3 of their size: compress
+    # at 1e-3, a coarse factorisation that only preconditions
+    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf, length=w.length, tf32=True, factor_tol=1e-3)
+    A.aifmm_factor(h)
+    xo, K = _h2_solution(w, pts, b)
+    x1 = A.aifmm_solve(h, b)[:, 0]
+    e1 = _rel(x1, xo)
+    assert 1e-8 < e1 <= 0.5, e1
+    x, it, rr = A.aifmm_gmres(h, b, rtol=1e-11, maxit=100, restart=40, use_precond=True)
+    assert rr <= 1e-11
+    assert _rel(x, xo) <= 1e-9
+    _, it0, _ = A.aifmm_gmres(h, b, rtol=1e-11, maxit=600, restart=40, use_precond=False)
+    assert it0 > it, (it0, it)
+    A.aifmm_destroy(h)
