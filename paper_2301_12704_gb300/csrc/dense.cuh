@@ -271,7 +271,7 @@ __device__ inline void tile_gemm(const double* A, int lda, const double* B, int 
 // A22 -= L21 U12, and B2 -= L21 B1 for the right-hand columns; grid
 // (coltiles of A22 then of B, rowtiles, items); PM_FMA, PM_OZ8 or PM_F32
 template <int PM = PM_FMA>
-static __global__ void __launch_bounds__(256) k_lu_gemm(const LuItem* items, int k0) {
+static __global__ void __launch_bounds__(256, 2) k_lu_gemm(const LuItem* items, int k0) {
   LuItem it = items[blockIdx.z];
   int n = it.n;
   int kend = min(n, k0 + LU_NB);
@@ -581,7 +581,7 @@ static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) { ipiv_to_
 // trailing update after diagonal block k0: lower -> rows below, upper -> rows
 // above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)
 template <int LOWER, int PM = PM_FMA>
-static __global__ void __launch_bounds__(256) k_lus_update(const SolveItem* items, int k0) {
+static __global__ void __launch_bounds__(256, 2) k_lus_update(const SolveItem* items, int k0) {
   SolveItem it = items[blockIdx.z];
   int n = it.n;
   if (k0 >= n) return;
@@ -672,9 +672,11 @@ namespace aifmm {
 // column-major with ld h = n - k0).  Warp 0 searches the pivot and swaps the
 // two panel rows; then every thread scales and updates the rows it owns.
 // Interchanges outside the panel are applied afterwards by k_lu_laswp.
-// dynamic shared memory: (maxh * LU_NB) doubles; items with n - k0 > maxh are
-// skipped here (they take the global-memory panel path).
-static __global__ void __launch_bounds__(256) k_lu_panel_sm(const LuItem* items, int k0, int maxh, int* err) {
+// Any block size that is a multiple of 32 (lu_panel_threads: more threads
+// for taller panels, whose rank-1 updates sit on the critical path of every
+// column step).  dynamic shared memory: (maxh * LU_NB) doubles; items with
+// n - k0 > maxh are skipped here (they take the global-memory panel path).
+static __global__ void __launch_bounds__(1024) k_lu_panel_sm(const LuItem* items, int k0, int maxh, int* err) {
   extern __shared__ double Ps[];
   __shared__ int sing;
   LuItem it = items[blockIdx.x];
@@ -765,6 +767,9 @@ static __global__ void __launch_bounds__(128) k_lu_laswp(const LuItem* items, in
     }
   }
 }
+
+// threads of k_lu_panel_sm for panels of up to h rows
+inline int lu_panel_threads(int h) { return h > 512 ? 1024 : h > 256 ? 512 : 256; }
 
 // global-memory panel for items too tall for shared memory
 static __global__ void __launch_bounds__(256) k_lu_panel_big(const LuItem* items, int k0, int maxh, int* err) {

@@ -610,7 +610,7 @@ __device__ inline int proj_cols(const Cmp& c, int t, int side, int nf0, int what
 
 // grid (tiles over X's columns, tiles over nf0, cnt * sides)
 template <int PM>
-__global__ void __launch_bounds__(256) k_cmp_ptq(LV v, Cmp c, int what) {
+__global__ void __launch_bounds__(256, 2) k_cmp_ptq(LV v, Cmp c, int what) {
   const int nsd = c.sym ? 1 : 2;
   const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
   if (c.skip[t]) return;
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(256) k_cmp_ptq(LV v, Cmp c, int what) {
 
 // grid (tiles over X's columns, tiles over m, cnt * sides)
 template <int PM>
-__global__ void __launch_bounds__(256) k_cmp_pqt(LV v, Cmp c, int what) {
+__global__ void __launch_bounds__(256, 2) k_cmp_pqt(LV v, Cmp c, int what) {
   const int nsd = c.sym ? 1 : 2;
   const int t = blockIdx.z / nsd, side = blockIdx.z % nsd;
   if (c.skip[t]) return;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(256) k_cmp_equalise(LV v, Cmp c) {
 // L_b = U~^T U_b (side 0), R_b = V~^T V_b (side 1); rn x r_old, ld R.
 // grid (tiles over r_old, tiles over rn, 2 * cnt); Lm zeroed beforehand
 template <int PM>
-__global__ void __launch_bounds__(256) k_cmp_lmat(LV v, Cmp c) {
+__global__ void __launch_bounds__(256, 2) k_cmp_lmat(LV v, Cmp c) {
   int t = blockIdx.z >> 1, side = blockIdx.z & 1;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256) k_cmp_row_transform(LV v, Cmp c) {
 // (the P2L block is zero before b is eliminated).  grid (ns5 * tpc, tiles
 // over rn, cnt) with tpc column tiles per block.
 template <int PM>
-__global__ void __launch_bounds__(256) k_cmp_row_fill(LV v, Cmp c, int tpc) {
+__global__ void __launch_bounds__(256, 2) k_cmp_row_fill(LV v, Cmp c, int tpc) {
   int s = blockIdx.x / tpc, tj = blockIdx.x % tpc, t = blockIdx.z;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_mirror(LV v, Cmp c) {
 // (the M2P block into y_b is zero before b is eliminated).
 // grid (ns5 * tpr, tiles over rn, cnt) with tpr row tiles per block.
 template <int PM>
-__global__ void __launch_bounds__(256) k_cmp_col_fill(LV v, Cmp c, int tpr) {
+__global__ void __launch_bounds__(256, 2) k_cmp_col_fill(LV v, Cmp c, int tpr) {
   int s = blockIdx.x / tpr, ti = blockIdx.x % tpr, t = blockIdx.z;
   if (c.skip[t]) return;
   int b = cbox(c, v, t);
@@ -1354,7 +1354,7 @@ __device__ __forceinline__ void schur_tile(const LV& v, const Elim& e, const Sch
 // tile, whose tensor-memory allocation a CTA may make once: there the grid
 // covers an upper bound of the list and each CTA takes at most one item.
 template <int PM>
-__global__ void __launch_bounds__(256) k_schur(LV v, Elim e, const SchurItem* __restrict__ items,
+__global__ void __launch_bounds__(256, PM == PM_TC05 ? 1 : 2) k_schur(LV v, Elim e, const SchurItem* __restrict__ items,
                                               const int* __restrict__ count, int sym) {
   extern __shared__ __align__(16) unsigned char ozs[];
   const int n = *count;
@@ -1768,7 +1768,6 @@ static int factor_level(Handle& h, int l) {
     k_z_build<<<dim3(ipow(3, d) + 1, cnt, ZB_SLICES), 256, 0, st>>>(v, e); ++h.nlaunch;
     dp.end();
     k_colmax<<<cnt, 256, 0, st>>>(e.lu, e.colmax, F.P); ++h.nlaunch;
-    dp.begin("lu");
     {
       // LU with partial pivoting of [Piv | B] (B = the coupled columns,
       // k_z_build): the interchanges, the panels' unit-lower solves and the
@@ -1782,12 +1781,21 @@ static int factor_level(Handle& h, int l) {
       const int tiles = (F.P + 63) / 64, ctiles = tiles + (e.ncmax + 63) / 64;
       for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
         const int hh = std::min(F.P - k0, maxh);
-        k_lu_panel_sm<<<cnt, 256, sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
+        dp.begin("lu_panel");
+        k_lu_panel_sm<<<cnt, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh,
+                                                                                              h.derr);
+        ++h.nlaunch;
         if (F.P - k0 > maxh) {
           k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
         }
+        dp.end();
+        dp.begin("lu_laswp");
         k_lu_laswp<<<dim3((ctot + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
+        dp.end();
+        dp.begin("lu_trsm");
         k_lu_trsm<<<dim3((ctot + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
+        dp.end();
+        dp.begin("lu_gemm");
         if (pm == PM_F32)
           k_lu_gemm<PM_F32><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         else if (pm == PM_TF32)
@@ -1797,10 +1805,10 @@ static int factor_level(Handle& h, int l) {
         else
           k_lu_gemm<PM_FMA><<<dim3(ctiles, tiles, cnt), 256, 0, st>>>(e.lu, k0);
         ++h.nlaunch;
+        dp.end();
       }
     }
     k_piv_perm<<<(cnt + 127) / 128, 128, 0, st>>>(v, col, cnt); ++h.nlaunch;
-    dp.end();
     delete gt;
     // ---- Z = U^-1 (L^-1 P B) and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
@@ -2002,7 +2010,9 @@ int run_factor(Handle& h) {
   k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
     const int hh = std::min(h.ntop - k0, h.panel_rows);
-    k_lu_panel_sm<<<1, 256, sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
+    k_lu_panel_sm<<<1, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows,
+                                                                                           h.derr);
+    ++h.nlaunch;
     if (h.ntop - k0 > h.panel_rows) {
       k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
     }

@@ -15,7 +15,7 @@ namespace aifmm {
 namespace {
 
 template <bool KB, int S>
-__global__ void __launch_bounds__(256) k_gemm_oz(const double* A, int64_t lda, const double* B, int64_t ldb,
+__global__ void __launch_bounds__(256, 2) k_gemm_oz(const double* A, int64_t lda, const double* B, int64_t ldb,
                                                  double* C, int64_t ldc, int m, int n, int k, double alpha) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;

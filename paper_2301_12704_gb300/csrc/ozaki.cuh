@@ -22,10 +22,10 @@
 //    of K stay below 5 * 32 * 2^14 < 2^22 and are exact; the pairs with
 //    s + t = 5..8 (weight 2^-35 and below) share one FP32 accumulator whose
 //    truncation stays near 2^-54 of the tile's scale;
-//  * every 32 of K the exact weights are summed into one 64-bit integer and
-//    the rest into FP32; once per K chunk (two such halves, one set of row
-//    and column exponents) the two are added in FP64 and the result scaled
-//    by 2^(E_row + E_col) into the FP64 result registers.
+//  * once per K chunk of 32 (one set of row and column exponents) the exact
+//    weights are summed into one 64-bit integer and the rest into FP32, the
+//    two added in FP64 and the result scaled by 2^(E_row + E_col) into the
+//    FP64 result registers.
 // Pairs with s + t > 8 are dropped: a digit pair contributes up to 2^14 times
 // its weight, so s + t = 7, 8 still matter at the 2^-48 level while s + t >= 9
 // is below 2^-49 of the top digits' product: 39 digit-pair MMAs per 16-deep
@@ -33,7 +33,8 @@
 // FP64-size error relative to |A| |B| rows and columns of moderate dynamic
 // range; an entry 2^-d below its row's (column's) largest in a chunk keeps
 // 49 - d bits.
-// 256 threads (8 warps, each a 32 x 16 sub-tile: 2 x 2 MMAs of m16n8k16).
+// 256 threads (8 warps; per 32-column half of the tile each warp a 16 x 16
+// sub-tile: 2 MMAs of m16n8k16 per digit pair and 16 of K).
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -41,10 +42,10 @@
 namespace aifmm {
 
 constexpr int OZ_S = 7;                // digits per operand
-constexpr int OZ_KC = 64;              // K chunk
-constexpr int OZ_LD = OZ_KC + 8;       // padded smem row (bf16 elements): conflict-free fragment loads
+constexpr int OZ_KC = 32;              // K chunk
+constexpr int OZ_LD = OZ_KC + 8;       // padded smem row (bf16 elements, 20 words): conflict-free fragment loads
 // bytes of dynamic shared memory of the tile with S digits per operand
-constexpr int oz_smem(int S) { return 2 * S * 64 * OZ_LD * 2 + 3 * 64 * 4; }
+constexpr int oz_smem(int S) { return S * (64 + 32) * OZ_LD * 2 + 3 * 64 * 4; }
 constexpr int OZ_SMEM = oz_smem(OZ_S);
 constexpr int OZ_S8 = 8;               // digits of the high-precision variant
 constexpr int OZ_SMEM8 = oz_smem(OZ_S8);
@@ -111,139 +112,119 @@ __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
 // are unchanged (only exponents move), but rows of B of very different
 // magnitudes -- the x and z parts of a column of Piv^-1 B -- no longer lose
 // the small rows' digits to the large rows' exponent.
+//
+// Layout: the tile's two 32-column halves in turn (a half that lies beyond
+// nc is skipped), each over K in chunks of OZ_KC = 32 with one set of row
+// and column exponents per chunk (KB: the balancing binades over the half's
+// columns).  Per chunk the digit planes of A (S x 64 rows) and of the half of
+// B (S x 32 columns) are staged, then each warp computes a 16 x 16 sub-tile
+// of the half (m16n8k16, two n8 blocks).  Only one half's digit-pair
+// accumulators and FP64 results are live, so a thread needs at most 128
+// registers and a CTA 54 KB (S = 7) or 62 KB (S = 8) of shared memory: two
+// CTAs share an SM and hide each other's staging and MMA latencies.
 template <bool TA = false, bool KB = false, int S = OZ_S>
 __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                        int mr, int nc, int K, double alpha, unsigned char* smem) {
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [S][64][OZ_LD]
-  __nv_bfloat16* Bs = As + S * 64 * OZ_LD;                               // [S][64][OZ_LD] (col, k)
-  int* ea = reinterpret_cast<int*>(Bs + S * 64 * OZ_LD);                 // [64] row exponents
-  int* eb = ea + 64;                                                     // [64] column exponents
-  int* ek = eb + 64;                                                     // [64] KB: binade of row k of B
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [S][64][OZ_LD] (row, k)
+  __nv_bfloat16* Bs = As + S * 64 * OZ_LD;                               // [S][32][OZ_LD] (column of the half, k)
+  int* ea = reinterpret_cast<int*>(Bs + S * 32 * OZ_LD);                 // [64] row exponents
+  int* eb = ea + 64;                                                     // [64] column exponents (32 used)
+  int* ek = eb + 64;                                                     // [64] KB: binade of row k of B (32 used)
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wr = (w & 1) * 32, wc = (w >> 1) * 16;                       // warp sub-tile origin
   const int g = lane >> 2, cq = lane & 3;
-  double acc64[2][2][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
+  const int wr = 16 * (w & 3);                                           // warp's rows
+  const int wc = 16 * (w >> 2);                                          // warp's columns in the half
+  for (int hc = 0; hc < 2; ++hc) {
+    const int jh = 32 * hc;                                              // first column of the half
+    if (jh >= nc) break;                                                 // the same for every thread
+    double acc64[2][4];                                                  // [n8 block][fragment]
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc64[a][b][q] = 0.0;
-
-  for (int k0 = 0; k0 < K; k0 += OZ_KC) {
-    const int kc = min(OZ_KC, K - k0);
-    // ---- stage: exponents (rows of op(A), columns of B over this chunk)
-    if (tid < 192) (tid < 64 ? ea : tid < 128 ? eb : ek)[tid & 63] = (KB && tid < 128) ? OZ_NEG : 0;
-    __syncthreads();
-    // B: warp w takes columns 8w..8w+7, lanes k = lane and lane + 32
-    double bv[8][2];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int j = 8 * w + q;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int k = lane + 32 * h;
-        bv[q][h] = (j < nc && k < kc) ? B[(k0 + k) + (size_t)j * ldb] : 0.0;
-      }
-    }
-    if (KB) {
-      int r0 = 0, r1 = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        r0 = max(r0, oz_bexp(bv[q][0]));
-        r1 = max(r1, oz_bexp(bv[q][1]));
-      }
-      atomicMax(&ek[lane], r0);
-      atomicMax(&ek[lane + 32], r1);
+      for (int q = 0; q < 4; ++q) acc64[b][q] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += OZ_KC) {
+      const int kc = min(OZ_KC, K - k0);
+      // ---- stage: exponents (rows of op(A), columns of the half over this chunk)
+      if (tid < 192) (tid < 64 ? ea : tid < 128 ? eb : ek)[tid & 63] = (KB && tid < 128) ? OZ_NEG : 0;
       __syncthreads();
-    }
-    // exponent of an entry after the shift of its k (KB: d_k = ek[k] - 1023,
-    // + for A, - for B); zero entries take no part in a maximum
-    auto vexp = [&](double x, int k, int sgn) -> int {
-      int e = oz_bexp(x);
-      if (!KB) return e;
-      return e == 0 ? OZ_NEG : e + sgn * (ek[k] - 1023);
-    };
+      // B: warp w takes the half's columns 4w..4w+3, lane the k
+      double bv[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int j = 8 * w + q;
-      int bm = KB ? OZ_NEG : 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) bm = max(bm, vexp(bv[q][h], lane + 32 * h, -1));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-      if (lane == 0) eb[j] = bm;
-    }
-    // A: warp w takes k = 8w..8w+7, lanes the rows lane and lane + 32 (with
-    // TA: warp w the rows 8w..8w+7, lanes k = lane and lane + 32, so that the
-    // loads stay coalesced)
-    double av[8][2];
-    if (!TA) {
-      int am0 = KB ? OZ_NEG : 0, am1 = KB ? OZ_NEG : 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        int k = 8 * w + q;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int i = lane + 32 * h;
-          double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
-          av[q][h] = x;
-          int e = vexp(x, k, 1);
-          if (h == 0) am0 = max(am0, e); else am1 = max(am1, e);
-        }
+      for (int q = 0; q < 4; ++q) {
+        const int j = jh + 4 * w + q;
+        bv[q] = (j < nc && lane < kc) ? B[(k0 + lane) + (size_t)j * ldb] : 0.0;
       }
-      atomicMax(&ea[lane], am0);
-      atomicMax(&ea[lane + 32], am1);
-    } else {
+      if (KB) {
+        int r = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        int i = 8 * w + q;
+        for (int q = 0; q < 4; ++q) r = max(r, oz_bexp(bv[q]));
+        atomicMax(&ek[lane], r);
+        __syncthreads();
+      }
+      // exponent of an entry after the shift of its k (KB: d_k = ek[k] - 1023,
+      // + for A, - for B); zero entries take no part in a maximum
+      auto vexp = [&](double x, int k, int sgn) -> int {
+        int e = oz_bexp(x);
+        if (!KB) return e;
+        return e == 0 ? OZ_NEG : e + sgn * (ek[k] - 1023);
+      };
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int bm = vexp(bv[q], lane, -1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        if (lane == 0) eb[4 * w + q] = bm;
+      }
+      // A: without TA, lane + 32 (w / 4) is the row and 8 (w % 4).. + 7 the k
+      // (one 16-byte digit store per row later); with TA, warp w takes the
+      // rows 8w..8w+7 and lane the k, so that the loads stay coalesced
+      double av[8];
+      if (!TA) {
+        const int i = lane + 32 * (w >> 2), kb0 = 8 * (w & 3);
         int am = KB ? OZ_NEG : 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int k = lane + 32 * h;
-          double x = (i < mr && k < kc) ? A[(k0 + k) + (size_t)i * lda] : 0.0;
-          av[q][h] = x;
+        for (int q = 0; q < 8; ++q) {
+          const int k = kb0 + q;
+          const double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
+          av[q] = x;
           am = max(am, vexp(x, k, 1));
         }
+        atomicMax(&ea[i], am);
+      } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
-        if (lane == 0) ea[i] = am;
-      }
-    }
-    __syncthreads();
-    // ---- stage: digits into shared memory (B first: its registers are free
-    // before the A digits are packed)
+        for (int q = 0; q < 8; ++q) {
+          const int i = 8 * w + q;
+          const double x = (i < mr && lane < kc) ? A[(k0 + lane) + (size_t)i * lda] : 0.0;
+          av[q] = x;
+          int am = vexp(x, lane, 1);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int j = 8 * w + q;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int k = lane + 32 * h;
-        oz_digits<S>(bv[q][h], KB ? eb[j] + (ek[k] - 1023) : eb[j], Bs + j * OZ_LD + k, 64 * OZ_LD);
-      }
-    }
-    if (TA) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int i = 8 * w + q, k = lane + 32 * h;
-          oz_digits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], As + i * OZ_LD + k, 64 * OZ_LD);
+          for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+          if (lane == 0) ea[i] = am;
         }
       }
-    } else {
-      // a lane holds k = 8w..8w+7 of its row: one 16-byte store per digit
-      // (rows 144 bytes apart: eight lanes cover the 32 banks once)
+      __syncthreads();
+      // ---- stage: digits into shared memory
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
+      for (int q = 0; q < 4; ++q) {
+        const int jl = 4 * w + q;
+        oz_digits<S>(bv[q], KB ? eb[jl] + (ek[lane] - 1023) : eb[jl], Bs + jl * OZ_LD + lane, 32 * OZ_LD);
+      }
+      if (TA) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = 8 * w + q;
+          oz_digits<S>(av[q], KB ? ea[i] - (ek[lane] - 1023) : ea[i], As + i * OZ_LD + lane, 64 * OZ_LD);
+        }
+      } else {
+        // a lane holds k = kb0..kb0+7 of its row: one 16-byte store per
+        // digit (rows 80 bytes apart)
+        const int i = lane + 32 * (w >> 2), kb0 = 8 * (w & 3);
         uint32_t pk[S][4];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int k = 8 * w + q;
+          const int k = kb0 + q;
           uint16_t d[S];
-          oz_digit_bits<S>(av[q][h], KB ? ea[i] - (ek[k] - 1023) : ea[i], d);
+          oz_digit_bits<S>(av[q], KB ? ea[i] - (ek[k] - 1023) : ea[i], d);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
             if (q & 1) pk[s][q >> 1] |= (uint32_t)d[s] << 16;
@@ -252,102 +233,78 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
         }
 #pragma unroll
         for (int s = 0; s < S; ++s)
-          *reinterpret_cast<uint4*>(As + s * 64 * OZ_LD + i * OZ_LD + 8 * w) =
+          *reinterpret_cast<uint4*>(As + s * 64 * OZ_LD + i * OZ_LD + kb0) =
               make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
       }
-    }
-    __syncthreads();
-    // ---- MMAs, flushed every 32 of K: digit-pair weights s + t = 0..4 each
-    // in its own accumulator (exact), 5..8 together.  The two halves of a
-    // chunk share the row and column scales, so the exact part is carried
-    // from the first to the second as a 64-bit integer (and the rest as
-    // FP32) and converted and scaled in FP64 once per chunk.
-    long long tot[2][2][4];
-    float r5[2][2][4];
-    for (int kh = 0; kh < OZ_KC; kh += 32) {
-      const bool first = kh == 0;
-      float acc[6][2][2][4];
+      __syncthreads();
+      // ---- MMAs: digit-pair weights s + t = 0..4 each in its own
+      // accumulator (exact: at most 5 pairs x 32 of K x 2^14 < 2^22 per
+      // weight), 5..8 together in FP32; recombined once per chunk, the exact
+      // part as a 64-bit integer in units of 2^-28, then scaled by the row
+      // and column exponents in FP64
+      float acc[6][2][4];
 #pragma unroll
       for (int x = 0; x < 6; ++x)
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-          for (int b = 0; b < 2; ++b)
+          for (int q = 0; q < 4; ++q) acc[x][b][q] = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[x][a][b][q] = 0.f;
-#pragma unroll
-      for (int kk = kh; kk < kh + 32; kk += 16) {
+      for (int kk = 0; kk < OZ_KC; kk += 16) {
         uint32_t bf[S][2][2];
 #pragma unroll
         for (int t = 0; t < S; ++t)
 #pragma unroll
           for (int b = 0; b < 2; ++b) {
-            const __nv_bfloat16* base = Bs + t * 64 * OZ_LD + (wc + 8 * b + g) * OZ_LD + kk + 2 * cq;
+            const __nv_bfloat16* base = Bs + t * 32 * OZ_LD + (wc + 8 * b + g) * OZ_LD + kk + 2 * cq;
             bf[t][b][0] = *reinterpret_cast<const uint32_t*>(base);
             bf[t][b][1] = *reinterpret_cast<const uint32_t*>(base + 8);
           }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          uint32_t af[2][4];
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            const __nv_bfloat16* base = As + s * 64 * OZ_LD + (wr + 16 * a + g) * OZ_LD + kk + 2 * cq;
-            af[a][0] = *reinterpret_cast<const uint32_t*>(base);
-            af[a][1] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD);
-            af[a][2] = *reinterpret_cast<const uint32_t*>(base + 8);
-            af[a][3] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD + 8);
-          }
+          uint32_t af[4];
+          const __nv_bfloat16* base = As + s * 64 * OZ_LD + (wr + g) * OZ_LD + kk + 2 * cq;
+          af[0] = *reinterpret_cast<const uint32_t*>(base);
+          af[1] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD);
+          af[2] = *reinterpret_cast<const uint32_t*>(base + 8);
+          af[3] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD + 8);
 #pragma unroll
           for (int t = 0; t < S; ++t) {
             if (s + t > S + 1) continue;        // s + t > S + 1: dropped
             const int grp = min(s + t, 5);
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-              for (int b = 0; b < 2; ++b) oz_mma(acc[grp][a][b], af[a], bf[t][b]);
+            for (int b = 0; b < 2; ++b) oz_mma(acc[grp][b], af, bf[t][b]);
           }
         }
       }
-      // ---- recombine: the exact weights as one 64-bit integer in units of
-      // 2^-28, the rest in FP32; after the second half the row and column
-      // scales in FP64
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < 4; ++q) {
+          long long tt = 0;
+          float wgt = 1.0f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            long long t = first ? 0 : tot[a][b][q];
-            float wgt = 1.0f;
-#pragma unroll
-            for (int x = 0; x < 5; ++x) {
-              t += (long long)__float2int_rn(acc[x][a][b][q] * wgt) * (1ll << (7 * (4 - x)));
-              wgt *= 128.0f;
-            }
-            if (first) {
-              tot[a][b][q] = t;
-              r5[a][b][q] = acc[5][a][b][q];
-            } else {
-              int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
-              double sum = fma((double)t, 0x1p-28, (double)(acc[5][a][b][q] + r5[a][b][q]));
-              // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
-              int be = ea[i] + eb[j] - 2058 + 1023;
-              double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
-              acc64[a][b][q] = fma(sum, sc, acc64[a][b][q]);
-            }
+          for (int x = 0; x < 5; ++x) {
+            tt += (long long)__float2int_rn(acc[x][b][q] * wgt) * (1ll << (7 * (4 - x)));
+            wgt *= 128.0f;
           }
+          const int i = wr + g + 8 * (q >> 1), jl = wc + 8 * b + 2 * cq + (q & 1);
+          const double sum = fma((double)tt, 0x1p-28, (double)acc[5][b][q]);
+          // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
+          const int be = ea[i] + eb[jl] - 2058 + 1023;
+          const double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
+          acc64[b][q] = fma(sum, sc, acc64[b][q]);
+        }
+      __syncthreads();   // the next chunk overwrites the planes and exponents
     }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        int i = wr + 16 * a + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
-        if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc64[a][b][q];
+        const int i = wr + g + 8 * (q >> 1), j = jh + wc + 8 * b + 2 * cq + (q & 1);
+        if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc64[b][q];
       }
+  }
 }
 
 }  // namespace aifmm
