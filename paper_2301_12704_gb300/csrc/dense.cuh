@@ -56,6 +56,51 @@ static __global__ void __launch_bounds__(128) k_lu_trsm(const LuItem* items, int
   if (lane < nb) X[lane] = x;
 }
 
+// The same U12 = L11^-1 A12 with one thread per column, its 32 entries in
+// registers and L broadcast from shared memory.  Every FP64 lane does useful
+// work (496 warp FMAs per 32 columns against 1024 lane slots per column in
+// the warp form, half of them masked), at the price of a longer chain per
+// thread; each entry sees the same FMAs in the same order as in the warp
+// form, so the results are equal bit for bit.  grid (column groups of
+// blockDim.x, items), 32 to 128 threads.
+static __global__ void __launch_bounds__(128) k_lu_trsm_t(const LuItem* items, int k0) {
+  __shared__ double L[LU_NB][LU_NB + 1];
+  LuItem it = items[blockIdx.y];
+  int n = it.n;
+  if (k0 >= n) return;
+  int kend = min(n, k0 + LU_NB), nb = kend - k0;
+  const double* A = it.a;
+  const int ld = it.ld;
+  for (int e = threadIdx.x; e < LU_NB * LU_NB; e += blockDim.x) {
+    int i = e % LU_NB, j = e / LU_NB;
+    L[i][j] = (i < nb && j < nb) ? A[(k0 + i) + (size_t)(k0 + j) * ld] : 0.0;
+  }
+  __syncthreads();
+  int c = kend + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n + it.nb) return;
+  double* X = lu_col(it, c) + k0;
+  double x[LU_NB];
+#pragma unroll
+  for (int i = 0; i < LU_NB; ++i) x[i] = i < nb ? X[i] : 0.0;
+#pragma unroll
+  for (int j = 0; j < LU_NB; ++j)
+#pragma unroll
+    for (int i = j + 1; i < LU_NB; ++i) x[i] -= L[i][j] * x[j];
+#pragma unroll
+  for (int i = 0; i < LU_NB; ++i)
+    if (i < nb) X[i] = x[i];
+}
+
+// Threads per CTA of the thread-per-column trsm for `cols` columns in one
+// launch (at capacity), or 0 for the warp form.  The thread form issues half
+// the FP64 warp instructions but runs 496 dependent-ish FMAs per warp, and an
+// FP64 warp instruction holds its SM sub-partition's pipe for many clocks, so
+// it pays only with several warps per sub-partition: measured at 65,536
+// points, 22% faster on the leaf level (over a hundred boxes per launch, about
+// 1,000 columns each at capacity) and slower on the levels above (at most 28
+// boxes per launch).
+inline int lu_trsm_threads(long long cols) { return cols < 98304 ? 0 : 128; }
+
 // narrow right operand (nc <= 8 columns, e.g. a single right-hand side):
 // 64 rows x 4 slices of K, one thread per (row, slice), every column of B
 // in registers; the slices are summed through shared memory

@@ -215,7 +215,11 @@ struct Cmp {
   int ccap;            // k_cmp_qrcp: column capacity of the phase (shared-memory norms)
   double eps;
   double* flops;       // device accumulator of algorithmic flops (compress group)
+  double* qflops;      // the same for the QR steps (k_cmp_qrcp and the basis QR)
   int* err;
+  int all;             // 1: t runs over every box of the level (Morton order), not one colour
+  const double* QB;    // [nb][2][M*M] Q0 of every box's basis, factored when the level starts
+                       // (k_cmp_qrcp phase 1 over all boxes); k_cmp_gather copies it into Q
   int sym;             // 1: A = A^T, side 1 is never gathered or factored and
                        // V~_b = U~_b (the column fill-ins are the transposed row
                        // fill-ins, so both RRQRs would see the same matrix)
@@ -230,7 +234,7 @@ __device__ inline double* qbase(const Cmp& c, int t, int side, int M) {
 // path; they are only ever modified with atomics
 __device__ inline unsigned ldflag(const unsigned* p) { return __ldcg(p); }
 
-__device__ inline int cbox(const Cmp& c, const LV& v, int t) { return colour_box(c.col, t, v.d, v.l); }
+__device__ inline int cbox(const Cmp& c, const LV& v, int t) { return c.all ? t : colour_box(c.col, t, v.d, v.l); }
 
 // pending well-separated fill-in of box b at stencil slot s, for one side:
 // side 0 -> the block in row X_b (P2P_bq in XX if q is not yet eliminated,
@@ -313,14 +317,21 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
   const int mb = v.m[b], rb = c.rold[t];
   double* W = c.W + ((size_t)t * 2 + side) * v.M * c.WC;
   int off, ncol;
+  const double* nsrc;   // the copied columns, for their norms (ld M)
   if (blockIdx.y == 0) {
+    // the basis: its Householder Q0 was factored when the level started
+    // (the basis of a box changes only at its own compression); W keeps
+    // no copy of U_b, whose norms enter the threshold
     const double* base = side == 0 ? v.u(b) : v.v(b);
+    const double* q0 = c.QB + ((size_t)b * 2 + side) * v.M * v.M;
+    double* Q = c.Q + ((size_t)t * 2 + side) * v.M * v.M;
     for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
       int i = e % mb, j = e / mb;
-      W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
+      Q[i + (size_t)j * v.M] = q0[i + (size_t)j * v.M];
     }
     off = 0;
     ncol = rb;
+    nsrc = base;
   } else {
     const int sl = blockIdx.y - 1;
     off = c.boff[((size_t)t * 2 + side) * v.ns5 + sl];
@@ -334,6 +345,7 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
       else W[j + (size_t)(off + i) * v.M] = w.src[i + (size_t)j * w.ld];
     }
     ncol = side == 0 ? w.cols : w.rows;
+    nsrc = W + (size_t)off * v.M;
   }
   __syncthreads();
   // largest squared column norm of the copied columns (m_b rows each)
@@ -342,7 +354,7 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
   for (int j = wp; j < ncol; j += 8) {
     double a = 0.0;
     for (int i = lane; i < mb; i += 32) {
-      const double x = W[i + (size_t)(off + j) * v.M];
+      const double x = nsrc[i + (size_t)j * v.M];
       a += x * x;
     }
     mx = fmax(mx, warp_sum(a));
@@ -357,18 +369,54 @@ __global__ void k_cmp_gather(LV v, Cmp c, int nsides) {
   }
 }
 
+// boxes with nothing pending skip the compression; the others are charged
+// the flops of their basis QR (factored for every box when the level
+// started: QR and explicit Q, 8 (m - k)(r - k) per column k and side)
 __global__ void k_cmp_skip(LV v, Cmp c) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= c.cnt) return;
   int b = cbox(c, v, t);
   int rb = v.r[b];
-  c.skip[t] = (v.m[b] == 0 || (c.nc[2 * t] == rb && (c.sym || c.nc[2 * t + 1] == rb))) ? 1 : 0;
+  const int m = v.m[b];
+  const int sk = (m == 0 || (c.nc[2 * t] == rb && (c.sym || c.nc[2 * t + 1] == rb))) ? 1 : 0;
+  c.skip[t] = sk;
+  if (!sk) {
+    double f = 0.0;
+    for (int k = 0; k < min(m, rb); ++k) f += 8.0 * (m - k) * (double)(rb - k);
+    atomicAdd(c.qflops, f * (c.sym ? 1 : 2));
+  }
+}
+
+// the basis of every box of the level into W (U_b, side 0; V_b, side 1)
+// for the basis QR of the whole level; nc = rold = r_b, skip when there is
+// nothing to factor.  grid (nb * sides), 256 threads; c.all = 1
+__global__ void k_basis_gather(LV v, Cmp c, int nsides) {
+  const int t = blockIdx.x / nsides, side = blockIdx.x % nsides;
+  const int b = t;
+  const int mb = v.m[b], rb = v.r[b];
+  double* W = c.W + ((size_t)t * 2 + side) * v.M * c.WC;
+  const double* base = side == 0 ? v.u(b) : v.v(b);
+  for (int e = threadIdx.x; e < mb * rb; e += blockDim.x) {
+    int i = e % mb, j = e / mb;
+    W[i + (size_t)j * v.M] = base[i + (size_t)j * v.M];
+  }
+  if (threadIdx.x == 0) {
+    c.nc[t * 2 + side] = rb;
+    if (side == 0) {
+      c.rold[t] = rb;
+      c.skip[t] = (mb == 0 || rb == 0) ? 1 : 0;
+    }
+    c.tau[t * 2 + side] = 0.0;
+  }
 }
 
 // Column-space compression of [U_b | F] in three steps with the same result,
 // in exact arithmetic, as one Householder QR whose first r_b columns are
 // taken in order and whose later columns are pivoted (reading R3):
-//   phase 1  Householder QR of W[:, :nf] = U_b (nf = r_b, no pivoting): Q0;
+//   phase 1  Householder QR of W[:, :nf] = U_b (nf = r_b, no pivoting): Q0,
+//            for every box of a level in one launch when the level starts
+//            (c.all; the basis of a box is not modified before its own
+//            compression); k_cmp_gather copies Q0 into the colour's Q;
 //   k_cmp_ptq / k_cmp_pqt   F := F - Q0 (Q0^T F) as tiled GEMMs (the work
 //            that the forced reflectors did as rank-1 updates of every
 //            fill-in column);
@@ -594,9 +642,11 @@ __global__ void __launch_bounds__(1024) k_cmp_qrcp(LV v, Cmp c) {
       c.rk[t * 2 + side] = nf0 + rank;
       if (c.sym) c.rk[t * 2 + 1] = nf0 + rank;
     }
-    double f = 2.0 * m * (n - nf);
-    for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
-    atomicAdd(c.flops, f);
+    if (c.phase == 2) {   // phase 1's flops are charged by k_cmp_skip to the boxes compressed
+      double f = 2.0 * m * (n - nf);
+      for (int kk = 0; kk < rank; ++kk) f += 4.0 * (m - kk) * (double)(n - kk) + 4.0 * (m - kk) * (double)(rank - kk);
+      atomicAdd(c.qflops, f);
+    }
   }
 }
 
@@ -1600,6 +1650,34 @@ static void collect_group_times(Handle& h) {
   h.g_ev.clear();
 }
 
+// k_cmp_qrcp for c.cnt boxes (nsides each) in clusters of q CTAs; few
+// clusters (top levels): wider CTAs, fewer columns per warp
+static int launch_qrcp(Handle& h, const LV& v, const Cmp& c, int q, int nsides, const FacLevel& F) {
+  cudaLaunchConfig_t cfg = {};
+  const int ncta = q * nsides * c.cnt;
+  cfg.gridDim = dim3(ncta);
+  cfg.blockDim = dim3(ncta <= h.nsm ? 1024 : ncta <= 2 * h.nsm ? 512 : 256);
+  cfg.dynamicSmemBytes = sizeof(double) * (2 * (size_t)F.M + (F.M + 1) / 2 + 2 * (size_t)((c.ccap + q - 1) / q));
+  if (cfg.dynamicSmemBytes > (size_t)h.smem_optin) {
+    h.err = "compress: a box side needs " + std::to_string(cfg.dynamicSmemBytes) + " bytes of shared memory per CTA";
+    return HCAPACITY;
+  }
+  if (cfg.dynamicSmemBytes > 48 * 1024)
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)cfg.dynamicSmemBytes));
+  cfg.stream = h.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = q;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, c));
+  ++h.nlaunch;
+  return HOK;
+}
+
 static int factor_level(Handle& h, int l) {
   const int d = h.d;
   cudaStream_t st = h.stream;
@@ -1611,6 +1689,42 @@ static int factor_level(Handle& h, int l) {
   DetailProf dp;
   dp.on = std::getenv("AIFMM_PROFILE_DETAIL") != nullptr;
   dp.st = st;
+  const int nsides = h.sym ? 1 : 2;
+  // ---- Householder QR of every box's basis (phase 1 of the column-space
+  // compression) in one launch for the whole level: the basis of a box
+  // changes only at its own compression, so its Q0 is the same whichever
+  // colour step compresses it, and the colour steps no longer wait on a
+  // chain of dependent Householder steps each
+  double* QB = (double*)hscratch(h, 37, sizeof(double) * (size_t)F.nb * 2 * F.M * F.M);
+  {
+    Cmp cb = {};
+    cb.cnt = F.nb;
+    cb.all = 1;
+    cb.WC = F.R;
+    cb.W = (double*)hscratch(h, 38, sizeof(double) * (size_t)F.nb * 2 * F.M * F.R);
+    cb.Q = QB;
+    int* ib = (int*)hscratch(h, 39, sizeof(int) * (size_t)F.nb * 8);
+    cb.tau = (double*)hscratch(h, 40, sizeof(double) * (size_t)F.nb * 2);
+    if (!QB || !cb.W || !ib || !cb.tau) return HOOM;
+    cb.nc = ib;
+    cb.rk = ib + 2 * F.nb;
+    cb.rn = ib + 4 * F.nb;
+    cb.rold = ib + 5 * F.nb;
+    cb.skip = ib + 6 * F.nb;
+    cb.eps = h.ftol;
+    cb.flops = h.dacc;
+    cb.qflops = h.dacc + 1;
+    cb.err = h.derr;
+    cb.sym = h.sym ? 1 : 0;
+    cb.phase = 1;
+    cb.ccap = F.R;
+    dp.begin("qr_basis");
+    k_basis_gather<<<F.nb * nsides, 256, 0, st>>>(v, cb, nsides); ++h.nlaunch;
+    GroupTimer gq(h, Handle::G_QRCP);
+    const int rc = launch_qrcp(h, v, cb, 2, nsides, F);
+    if (rc != HOK) return rc;
+    dp.end();
+  }
   for (int col = 0; col < ncol; ++col) {
     int cnt = colour_count(col, d, F.n);
     if (cnt == 0) continue;
@@ -1620,9 +1734,11 @@ static int factor_level(Handle& h, int l) {
     c.cnt = cnt;
     c.eps = h.ftol;
     c.flops = h.dacc;
+    c.qflops = h.dacc + 1;   // the QR steps' flops are counted apart
     c.err = h.derr;
     c.sym = h.sym ? 1 : 0;
-    const int nsides = h.sym ? 1 : 2;
+    c.all = 0;
+    c.QB = QB;
     c.WC = F.R + nws * F.M;
     size_t wsz = (size_t)cnt * 2 * F.M * c.WC;
     c.W = (double*)hscratch(h, 20, sizeof(double) * wsz);
@@ -1646,58 +1762,34 @@ static int factor_level(Handle& h, int l) {
     dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
     {
-      // phase 1 (QR of U_b) in clusters of two CTAs; phase 2 (QRCP of the
-      // projected fill-ins) in clusters of qc CTAs, qc so that the colour's
-      // clusters give about two CTAs per SM
+      // Q0 (the basis QR) was copied in by k_cmp_gather: the fill-ins
+      // projected off it, then phase 2 (QRCP of the projected fill-ins) in
+      // clusters of qc CTAs, qc so that the colour's clusters give about two
+      // CTAs per SM, then the new basis columns made orthogonal to Q0 once more
       int qc = 2;
       while (qc < 16 && qc * nsides * cnt < 2 * h.nsm) qc *= 2;
       int maxr = 1;
       for (int b = 0; b < F.nb; ++b) maxr = std::max(maxr, F.h_r[b]);
       const int ptiles_r = (maxr + 63) / 64;
-      for (int phase = 1; phase <= 2; ++phase) {
-        const int q = phase == 1 ? 2 : qc;
-        c.phase = phase;
-        c.ccap = phase == 1 ? F.R : c.WC;
-        cudaLaunchConfig_t cfg = {};
-        const int ncta = q * nsides * cnt;
-        cfg.gridDim = dim3(ncta);
-        // few clusters (top levels): wider CTAs, fewer columns per warp
-        cfg.blockDim = dim3(ncta <= h.nsm ? 1024 : ncta <= 2 * h.nsm ? 512 : 256);
-        cfg.dynamicSmemBytes =
-            sizeof(double) * (2 * (size_t)F.M + (F.M + 1) / 2 + 2 * (size_t)((c.ccap + q - 1) / q));
-        if (cfg.dynamicSmemBytes > (size_t)h.smem_optin) {
-          h.err = "compress: a box side needs " + std::to_string(cfg.dynamicSmemBytes) +
-                  " bytes of shared memory per CTA";
-          return HCAPACITY;
+      for (int what = 0; what <= 1; ++what) {
+        if (what == 1) {
+          c.phase = 2;
+          c.ccap = c.WC;
+          dp.begin("qrcp_fill");
+          delete gt;
+          gt = new GroupTimer(h, Handle::G_QRCP);
+          const int rc = launch_qrcp(h, v, c, qc, nsides, F);
+          if (rc != HOK) {
+            delete gt;
+            return rc;
+          }
+          delete gt;
+          gt = new GroupTimer(h, Handle::G_COMPRESS);
+          dp.end();
         }
-        if (cfg.dynamicSmemBytes > 48 * 1024)
-          AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_cmp_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)cfg.dynamicSmemBytes));
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = q;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        dp.begin(phase == 1 ? "qr_basis" : "qrcp_fill");
-        delete gt;
-        gt = new GroupTimer(h, Handle::G_QRCP);
-        {
-          Cmp cq = c;
-          cq.flops = h.dacc + 1;   // the pivoted QR's flops are counted apart
-          AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_cmp_qrcp, v, cq));
-        }
-        ++h.nlaunch;
-        delete gt;
-        gt = new GroupTimer(h, Handle::G_COMPRESS);
-        dp.end();
-        // phase 1 -> project the fill-ins; phase 2 -> the new basis columns
-        const int what = phase == 1 ? 0 : 1;
         const int ncx = what == 0 ? c.WC : F.M;
         const dim3 g1((ncx + 63) / 64, ptiles_r, cnt * nsides), g2((ncx + 63) / 64, (F.M + 63) / 64, cnt * nsides);
-        dp.begin(phase == 1 ? "project_fill" : "project_basis");
+        dp.begin(what == 0 ? "project_fill" : "project_basis");
         AIFMM_LAUNCH_PM(pm, k_cmp_ptq, g1, v, c, what);
         AIFMM_LAUNCH_PM(pm, k_cmp_pqt, g2, v, c, what);
         h.nlaunch += 2;
@@ -1793,7 +1885,17 @@ static int factor_level(Handle& h, int l) {
         k_lu_laswp<<<dim3((ctot + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
         dp.end();
         dp.begin("lu_trsm");
-        k_lu_trsm<<<dim3((ctot + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0); ++h.nlaunch;
+        {
+          // columns right of the panel, per item, at capacity: n + nb - kend
+          // with kend = min(n, k0 + LU_NB), n <= F.P, nb <= ncmax
+          const int cols = ctot - k0 - std::min(LU_NB, F.P - k0);
+          const int tt = lu_trsm_threads((long long)cnt * cols);
+          if (tt)
+            k_lu_trsm_t<<<dim3((cols + tt - 1) / tt, cnt), tt, 0, st>>>(e.lu, k0);
+          else
+            k_lu_trsm<<<dim3((ctot + 3) / 4, cnt), 128, 0, st>>>(e.lu, k0);
+          ++h.nlaunch;
+        }
         dp.end();
         dp.begin("lu_gemm");
         if (pm == PM_F32)
