@@ -539,11 +539,16 @@ static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items
       double x[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[c] = lane < kb ? xs[k0 + lane + c * n] : 0.0;
-      for (int j = 0; j < kb - 1; ++j) {
-        const double l = lane > j && lane < kb ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+      // the lane's row of the block's strictly lower part, loaded before the
+      // chain (independent loads, one memory latency instead of one per step)
+      double lr[32];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) x[c] -= l * __shfl_sync(0xffffffffu, x[c], j);
-      }
+      for (int j = 0; j < 32; ++j) lr[j] = lane > j && lane < kb ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 31; ++j)
+        if (j < kb - 1)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) x[c] -= lr[j] * __shfl_sync(0xffffffffu, x[c], j);
       if (lane < kb)
 #pragma unroll
         for (int c = 0; c < NC; ++c) xs[k0 + lane + c * n] = x[c];
@@ -553,10 +558,19 @@ static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items
       double acc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-      for (int j = 0; j < kb; ++j) {
-        const double l = A[i + (size_t)(k0 + j) * ld];
+      if (kb == 32) {   // full block: the 32 loads of the row issued together
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fma(l, xs[k0 + j + c * n], acc[c]);
+        for (int j = 0; j < 32; ++j) {
+          const double l = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fma(l, xs[k0 + j + c * n], acc[c]);
+        }
+      } else {
+        for (int j = 0; j < kb; ++j) {
+          const double l = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fma(l, xs[k0 + j + c * n], acc[c]);
+        }
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) xs[i + c * n] -= acc[c];
@@ -570,16 +584,22 @@ static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items
       double x[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[c] = lane < kb ? xs[k0 + lane + c * n] : 0.0;
-      // reciprocals of the block's diagonal, one per lane, before the chain
+      // reciprocals of the block's diagonal, one per lane, and the lane's
+      // row of the block's strictly upper part, loaded before the chain
       const double rdl = lane < kb ? 1.0 / A[(k0 + lane) + (size_t)(k0 + lane) * ld] : 0.0;
-      for (int j = kb - 1; j >= 0; --j) {
-        const double rd = __shfl_sync(0xffffffffu, rdl, j);
-        const double u = lane < j ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+      double ur[32];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const double xj = __shfl_sync(0xffffffffu, x[c], j) * rd;
-          if (lane == j) x[c] = xj;
-          x[c] -= u * xj;
+      for (int j = 0; j < 32; ++j) ur[j] = lane < j && j < kb ? A[(k0 + lane) + (size_t)(k0 + j) * ld] : 0.0;
+#pragma unroll
+      for (int j = 31; j >= 0; --j) {
+        if (j < kb) {
+          const double rd = __shfl_sync(0xffffffffu, rdl, j);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const double xj = __shfl_sync(0xffffffffu, x[c], j) * rd;
+            if (lane == j) x[c] = xj;
+            x[c] -= ur[j] * xj;
+          }
         }
       }
       if (lane < kb)
@@ -591,10 +611,19 @@ static __global__ void __launch_bounds__(256) k_lus_small(const SolveItem* items
       double acc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-      for (int j = 0; j < kb; ++j) {
-        const double u = A[i + (size_t)(k0 + j) * ld];
+      if (kb == 32) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fma(u, xs[k0 + j + c * n], acc[c]);
+        for (int j = 0; j < 32; ++j) {
+          const double u = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fma(u, xs[k0 + j + c * n], acc[c]);
+        }
+      } else {
+        for (int j = 0; j < kb; ++j) {
+          const double u = A[i + (size_t)(k0 + j) * ld];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fma(u, xs[k0 + j + c * n], acc[c]);
+        }
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) xs[i + c * n] -= acc[c];
