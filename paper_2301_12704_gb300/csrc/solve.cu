@@ -261,44 +261,93 @@ __global__ void k_bwd_prep(LV v, SV s, int col, YSrc y, SolveItem* items) {
   }
 }
 
-// back substitution, step 2: w_x -= sum_q K_bq x_q + sum_r M2P_br y_r over the
-// neighbours; grid (row tiles, column tiles, cnt), the neighbours summed in
-// order inside each tile
-__global__ void __launch_bounds__(256) k_bwd_gemm(LV v, SV s, int col, YSrc y) {
+// neighbour o of box b for the backward products: its Morton index and
+// stencil slot, the block A (rows of b) and the right operand B (x_q, or
+// the multipoles y_q of an eliminated q); false if there is none
+__device__ inline bool bwd_term(const LV& v, const SV& s, int col, const YSrc& y, int b, int o, const double*& A,
+                                const double*& B, int& ldb, int& cols) {
+  int bc[3], q[3];
+  morton_coords(b, v.d, v.l, bc);
+  int oo = o;
+  for (int k = 0; k < 3; ++k) q[k] = bc[k];
+  for (int k = 0; k < v.d; ++k) {
+    q[k] = bc[k] + (oo % 3) - 1;
+    oo /= 3;
+  }
+  if (!in_grid(q, v.d, v.n)) return false;
+  int p = morton_key(q, v.d, v.l);
+  if (p == b) return false;
+  int sq = slot5(bc, q, v.d);
+  bool elim = colour_of(q, v.d) < col;
+  cols = elim ? v.r[p] : v.m[p];
+  if (cols == 0) return false;
+  A = elim ? v.xy(b, sq) : v.xx(b, sq);
+  if (elim) {
+    B = ybase(y, v.l, p, s.nrhs, ldb);
+  } else {
+    B = xx_(v, s, p);
+    ldb = v.M;
+  }
+  return true;
+}
+
+// back substitution, step 2: w_x -= sum_q K_bq x_q + sum_r M2P_br y_r over
+// the neighbours, in two launches: k_bwd_part computes every neighbour's
+// product P_o = K_bq x_q (or M2P_bq y_q) into its own zeroed block of Pb,
+// one CTA per (row tile, neighbour), so the neighbours' products run side by
+// side; k_bwd_sum then takes w_x += (-1) P_o over the neighbours in order
+// and clears Pb for the next colour.
+// Pb: [cnt][3^d][M x nrhs], ld M.  grid (row tiles * 3^d, column tiles, cnt)
+__global__ void __launch_bounds__(256) k_bwd_part(LV v, SV s, int col, YSrc y, int mt, double* __restrict__ Pb) {
+  int t = blockIdx.z;
+  int b = colour_box(col, t, v.d, v.l);
+  const int m = v.m[b], o = blockIdx.x / mt;
+  int i0 = (blockIdx.x % mt) * 64, j0 = blockIdx.y * 64;
+  if (i0 >= m || j0 >= s.nrhs) return;
+  const double* A;
+  const double* B;
+  int ldb, cols;
+  if (!bwd_term(v, s, col, y, b, o, A, B, ldb, cols)) return;
+  const int n3 = ipow(3, v.d);
+  double* P = Pb + ((size_t)t * n3 + o) * v.M * s.nrhs;
+  tile_gemm_64(A + i0, v.M, B + (size_t)j0 * ldb, ldb, P + i0 + (size_t)j0 * v.M, v.M, min(64, m - i0),
+               min(64, s.nrhs - j0), cols, 1.0);
+}
+
+// grid (row tiles, column tiles, cnt)
+__global__ void __launch_bounds__(256) k_bwd_sum(LV v, SV s, int col, YSrc y, double* __restrict__ Pb) {
   int t = blockIdx.z;
   int b = colour_box(col, t, v.d, v.l);
   const int m = v.m[b];
   int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
   if (i0 >= m || j0 >= s.nrhs) return;
   const int mr = min(64, m - i0), nc = min(64, s.nrhs - j0);
-  int bc[3], q[3];
-  morton_coords(b, v.d, v.l, bc);
+  const int n3 = ipow(3, v.d);
+  __shared__ unsigned live;
+  if (threadIdx.x == 0) {
+    unsigned f = 0;
+    for (int o = 0; o < n3 && o < 32; ++o) {
+      const double* A;
+      const double* B;
+      int ldb, cols;
+      if (bwd_term(v, s, col, y, b, o, A, B, ldb, cols)) f |= 1u << o;
+    }
+    live = f;
+  }
+  __syncthreads();
+  const unsigned f = live;
   double* w = ws(v, s, b);
-  int n3 = ipow(3, v.d);
-  for (int o = 0; o < n3; ++o) {
-    int oo = o;
-    for (int k = 0; k < 3; ++k) q[k] = bc[k];
-    for (int k = 0; k < v.d; ++k) {
-      q[k] = bc[k] + (oo % 3) - 1;
-      oo /= 3;
+  double* P = Pb + (size_t)t * n3 * v.M * s.nrhs;
+  for (int e = threadIdx.x; e < mr * nc; e += blockDim.x) {
+    const int i = i0 + e % mr, c = j0 + e / mr;
+    double acc = w[i + (size_t)c * v.P];
+    for (int o = 0; o < n3; ++o) {
+      if (!(f >> o & 1u)) continue;
+      double* po = P + (size_t)o * v.M * s.nrhs + i + (size_t)c * v.M;
+      acc += -1.0 * *po;
+      *po = 0.0;
     }
-    if (!in_grid(q, v.d, v.n)) continue;
-    int p = morton_key(q, v.d, v.l);
-    if (p == b) continue;
-    int sq = slot5(bc, q, v.d);
-    bool elim = colour_of(q, v.d) < col;
-    int cols = elim ? v.r[p] : v.m[p];
-    if (cols == 0) continue;
-    const double* A = elim ? v.xy(b, sq) : v.xx(b, sq);
-    int ldb;
-    const double* B;
-    if (elim) {
-      B = ybase(y, v.l, p, s.nrhs, ldb);
-    } else {
-      B = xx_(v, s, p);
-      ldb = v.M;
-    }
-    tile_gemm_64(A + i0, v.M, B + (size_t)j0 * ldb, ldb, w + i0 + (size_t)j0 * v.P, v.P, mr, nc, cols, -1.0);
+    w[i + (size_t)c * v.P] = acc;
   }
 }
 
@@ -501,7 +550,22 @@ struct SolveBufs {
   double* ytop;
   int* toff;
   SolveItem* items;   // max boxes of a colour + 1
+  double* part;       // backward products per neighbour, zero between colour steps (part_doubles)
 };
+
+// doubles of SolveBufs::part: the largest colour of any level x 3^d
+// neighbour blocks of M x nrhs
+static size_t part_doubles(const Handle& h, int nrhs) {
+  size_t mx = 0;
+  const int ncol = ipow(3, h.d);
+  for (int l = 2; l <= h.L; ++l) {
+    const FacLevel& F = h.fac[l];
+    int cmax = 0;
+    for (int col = 0; col < ncol; ++col) cmax = std::max(cmax, colour_count(col, h.d, F.n));
+    mx = std::max(mx, (size_t)cmax * ncol * F.M * nrhs);
+  }
+  return std::max(mx, (size_t)1);
+}
 
 // number of solve items needed: the largest colour of any level, plus the top
 static size_t solve_items(const Handle& h) {
@@ -565,7 +629,8 @@ static int sweeps(Handle& h, SolveBufs& B, double* b, int nrhs, int64_t ld) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
       k_bwd_prep<<<cnt, 256, 0, st>>>(v, sv[l], col, y, B.items); ++h.nlaunch;
-      k_bwd_gemm<<<dim3(mt, ct, cnt), 256, 0, st>>>(v, sv[l], col, y); ++h.nlaunch;
+      k_bwd_part<<<dim3(mt * ncol, ct, cnt), 256, 0, st>>>(v, sv[l], col, y, mt, B.part); ++h.nlaunch;
+      k_bwd_sum<<<dim3(mt, ct, cnt), 256, 0, st>>>(v, sv[l], col, y, B.part); ++h.nlaunch;
       lus_apply(h, B.items, cnt, F.P, nrhs, 1, st);
       k_bwd_out<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
     }
@@ -618,7 +683,10 @@ int run_solve(Handle& h, double* b, int nrhs, int64_t ld) {
   B.ytop = (double*)hscratch(h, 99, sizeof(double) * (size_t)nt * nrhs);
   B.toff = (int*)hscratch(h, 98, sizeof(int) * (h.top_off.size()));
   B.items = (SolveItem*)hscratch(h, 97, sizeof(SolveItem) * solve_items(h));
-  if (!B.ytop || !B.toff || !B.items) return HOOM;
+  const size_t npart = part_doubles(h, nrhs);
+  B.part = (double*)hscratch(h, 96, sizeof(double) * npart);
+  if (!B.ytop || !B.toff || !B.items || !B.part) return HOOM;
+  AIFMM_CUDA_TRY(h, cudaMemsetAsync(B.part, 0, sizeof(double) * npart, st));
   return sweeps(h, B, b, nrhs, ld);
 }
 
@@ -742,7 +810,8 @@ int run_solve_noalloc(Handle& h, double* b, int nrhs, int64_t ld) {
     size_t nb = F.nb;
     need += round(nb * F.M * nrhs) * 2 + round(nb * F.R * nrhs) + round(nb * F.P * nrhs);
   }
-  need += round((size_t)nt * nrhs) + round(h.top_off.size()) + nitem;
+  const size_t npart = part_doubles(h, nrhs);
+  need += round((size_t)nt * nrhs) + round(h.top_off.size()) + nitem + round(npart);
   if (need > NOALLOC_SCRATCH_DOUBLES) {
     h.err = "aifmm_solve_noalloc: this problem needs " + std::to_string(need * sizeof(double)) +
             " bytes of solve vectors for nrhs=" + std::to_string(nrhs) + "; the static scratch holds " +
@@ -774,6 +843,9 @@ int run_solve_noalloc(Handle& h, double* b, int nrhs, int64_t ld) {
   B.toff = reinterpret_cast<int*>(base + off);
   off += round(h.top_off.size());
   B.items = reinterpret_cast<SolveItem*>(base + off);
+  off += nitem;
+  B.part = base + off;   // must start at zero: the array keeps the previous call's contents
+  AIFMM_CUDA_TRY(h, cudaMemsetAsync(B.part, 0, sizeof(double) * npart, st));
   return sweeps(h, B, b, nrhs, ld);
 }
 
