@@ -821,6 +821,112 @@ static __global__ void __launch_bounds__(1024) k_lu_panel_sm(const LuItem* items
   }
 }
 
+// The same panel with every row in one thread's registers, for panels of at
+// most LU_RG_MAXH rows (one thread per row).  Rows never move: a thread
+// tracks the position of its row under the LAPACK interchanges (the pivot
+// row takes position jj, the row at jj takes the pivot's) and writes the
+// row to its final position at the end.  Per column one barrier: each warp
+// finds its best candidate (largest |a|, then the smallest position; the
+// bit patterns of non-negative doubles order as their values, so the
+// search is integer work) and its winning lane publishes the row and the
+// pivot's reciprocal in a double-buffered shared slot; after the barrier
+// every thread picks the block's winner from the warps' slots and updates
+// its row.  The multipliers and updates are the same operations as in
+// k_lu_panel_sm, and the interchanges the same, so the results are equal
+// bit for bit.  Singularity test as there, on bit patterns.  grid items,
+// blockDim a multiple of 32 covering n - k0 rows (at most LU_RG_MAXH).
+constexpr int LU_RG_MAXH = 512;
+static __global__ void __launch_bounds__(LU_RG_MAXH) k_lu_panel_rg(const LuItem* items, int k0, int* err) {
+  __shared__ long long ck[2][LU_RG_MAXH / 32];            // warp candidates: key
+  __shared__ int cp[2][LU_RG_MAXH / 32];                  // and position
+  __shared__ double crow[2][LU_RG_MAXH / 32][LU_NB + 1];  // their rows; [LU_NB]: 1 / pivot
+  __shared__ long long thr[LU_NB];                        // bits of 1e-14 x column maximum
+  const LuItem it = items[blockIdx.x];
+  const int n = it.n;
+  if (k0 >= n) return;
+  const int h = n - k0;
+  const int nbw = min(LU_NB, h);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  double* A = it.a;
+  const int ld = it.ld;
+  double a[LU_NB];
+#pragma unroll
+  for (int j = 0; j < LU_NB; ++j) a[j] = (t < h && j < nbw) ? A[(k0 + t) + (size_t)(k0 + j) * ld] : 0.0;
+  if (t < LU_NB) thr[t] = __double_as_longlong(1e-14 * ((it.colmax && t < nbw) ? it.colmax[k0 + t] : 0.0));
+  int pos = t;
+  bool live = t < h;   // not yet a pivot row
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < LU_NB; ++jj) {
+    if (jj < nbw) {
+      const int par = jj & 1;
+      long long key = -1;   // -1: no candidate (pivot rows, padding, NaN)
+      if (live) {
+        const long long kb = __double_as_longlong(fabs(a[jj]));
+        key = kb > 0x7ff0000000000000LL ? -1 : kb;
+      }
+      long long wk = key;
+      int wp = pos;
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, wk, o);
+        const int op = __shfl_xor_sync(0xffffffffu, wp, o);
+        if (ok > wk || (ok == wk && op < wp)) {
+          wk = ok;
+          wp = op;
+        }
+      }
+      if (wk >= 0 && pos == wp) {   // the warp's winning lane
+        double* cr = crow[par][w];
+#pragma unroll
+        for (int cc = 0; cc < LU_NB; ++cc)
+          if (cc >= jj) cr[cc] = a[cc];
+        cr[LU_NB] = 1.0 / a[jj];
+      }
+      if (lane == 0) {
+        ck[par][w] = wk;
+        cp[par][w] = wp;
+      }
+      __syncthreads();
+      long long bk = ck[par][0];
+      int bp = cp[par][0], bw = 0;
+      for (int u = 1; u < nw; ++u) {
+        const long long k2 = ck[par][u];
+        const int p2 = cp[par][u];
+        if (k2 > bk || (k2 == bk && p2 < bp)) {
+          bk = k2;
+          bp = p2;
+          bw = u;
+        }
+      }
+      // bk > thr: |pivot| > 1e-14 x column maximum; bk >= 2^52: a normal number
+      if (!(bk > thr[jj]) || !(bk >= 0x0010000000000000LL)) {
+        for (int q = jj + t; q < nbw; q += blockDim.x) it.ipiv[k0 + q] = k0 + q;
+        if (t == 0) set_err(err, DERR_SINGULAR);
+        return;
+      }
+      const double* pr = crow[par][bw];
+      if (live && pos == bp) {
+        it.ipiv[k0 + jj] = k0 + bp;
+        live = false;
+        pos = jj;
+      } else if (pos == jj) {
+        pos = bp;
+      }
+      if (live) {
+        const double l = a[jj] * pr[LU_NB];
+        a[jj] = l;
+#pragma unroll
+        for (int cc = 0; cc < LU_NB; ++cc)
+          if (cc > jj && cc < nbw) a[cc] -= l * pr[cc];
+      }
+    }
+  }
+  if (t < h)
+#pragma unroll
+    for (int j = 0; j < LU_NB; ++j)
+      if (j < nbw) A[(k0 + pos) + (size_t)(k0 + j) * ld] = a[j];
+}
+
 // the panel's interchanges applied to every column outside the panel
 // (left: the L factor, right: the part still to be factored, then B);
 // grid (colchunks over n + nb, items)

@@ -1874,11 +1874,16 @@ static int factor_level(Handle& h, int l) {
       for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
         const int hh = std::min(F.P - k0, maxh);
         dp.begin("lu_panel");
-        k_lu_panel_sm<<<cnt, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh,
-                                                                                              h.derr);
-        ++h.nlaunch;
-        if (F.P - k0 > maxh) {
-          k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
+        if (F.P - k0 <= LU_RG_MAXH) {
+          k_lu_panel_rg<<<cnt, (F.P - k0 + 31) / 32 * 32, 0, st>>>(e.lu, k0, h.derr);
+          ++h.nlaunch;
+        } else {
+          k_lu_panel_sm<<<cnt, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh,
+                                                                                                h.derr);
+          ++h.nlaunch;
+          if (F.P - k0 > maxh) {
+            k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
+          }
         }
         dp.end();
         dp.begin("lu_laswp");
@@ -2112,11 +2117,16 @@ int run_factor(Handle& h) {
   k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
     const int hh = std::min(h.ntop - k0, h.panel_rows);
-    k_lu_panel_sm<<<1, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows,
-                                                                                           h.derr);
-    ++h.nlaunch;
-    if (h.ntop - k0 > h.panel_rows) {
-      k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
+    if (h.ntop - k0 <= LU_RG_MAXH) {
+      k_lu_panel_rg<<<1, (h.ntop - k0 + 31) / 32 * 32, 0, st>>>(it, k0, h.derr);
+      ++h.nlaunch;
+    } else {
+      k_lu_panel_sm<<<1, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows,
+                                                                                             h.derr);
+      ++h.nlaunch;
+      if (h.ntop - k0 > h.panel_rows) {
+        k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
+      }
     }
     k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
     k_lu_trsm<<<dim3((h.ntop + 3) / 4, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
