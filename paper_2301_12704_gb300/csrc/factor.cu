@@ -67,7 +67,35 @@ LV view(Handle& h, FacLevel& F) {
 
 // ============================ level setup ====================================
 
-// leaf near field K_bq for q in N(b); grid (nb, 3^d)
+// The kernels are symmetric, K(x, y) = K(y, x), and keval gives bitwise
+// equal values for (i, j) and (j, i) (x_i - x_j is exactly -(x_j - x_i));
+// the near-field and interaction-list relations between boxes are
+// symmetric too.  So the set-up evaluates each pair of boxes once (the
+// block of the box with the smaller Morton index) and fills the partner's
+// block as its transpose (k_setup_*_mirror), with the same values.
+
+// dst (rows x cols, ld ldd) := src^T, src (cols x rows, ld lds), through a
+// 32 x 33 shared tile (both sides coalesced); every thread of the CTA calls it
+__device__ inline void copy_transposed(const double* __restrict__ src, int lds, double* __restrict__ dst, int ldd,
+                                       int rows, int cols) {
+  __shared__ double tile[32][33];
+  for (int i0 = 0; i0 < rows; i0 += 32)
+    for (int j0 = 0; j0 < cols; j0 += 32) {
+      for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int a = e & 31, b = e >> 5;
+        if (j0 + a < cols && i0 + b < rows) tile[b][a] = src[(j0 + a) + (size_t)(i0 + b) * lds];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int a = e & 31, b = e >> 5;
+        if (i0 + a < rows && j0 + b < cols) dst[(i0 + a) + (size_t)(j0 + b) * ldd] = tile[a][b];
+      }
+      __syncthreads();
+    }
+}
+
+// leaf near field K_bq for q in N(b) with b <= q (the rest: k_setup_leaf_K_mirror);
+// grid (nb, 3^d)
 __global__ void k_setup_leaf_K(LV v, const int* __restrict__ start, KParams kp, Pts P) {
   int b = blockIdx.x;
   int c[3], q[3];
@@ -81,6 +109,7 @@ __global__ void k_setup_leaf_K(LV v, const int* __restrict__ start, KParams kp, 
   }
   if (!in_grid(q, v.d, v.n)) return;
   int qb = morton_key(q, v.d, v.l);
+  if (qb < b) return;
   int s = slot5(c, q, v.d);
   int sb = start[b], mb = start[b + 1] - sb;
   int sq = start[qb], mq = start[qb + 1] - sq;
@@ -91,7 +120,27 @@ __global__ void k_setup_leaf_K(LV v, const int* __restrict__ start, KParams kp, 
   }
 }
 
-// M2L blocks A_bd = A(t^{b,i}, t^{d,i}) for d in IL(b); grid (nb, ns6)
+// K_bq = K_qb^T for the neighbours q < b; grid (nb, 3^d)
+__global__ void k_setup_leaf_K_mirror(LV v, const int* __restrict__ start) {
+  int b = blockIdx.x;
+  int c[3], q[3];
+  morton_coords(b, v.d, v.l, c);
+  int o = blockIdx.y;
+  for (int k = 0; k < 3; ++k) q[k] = c[k];
+  int oo = o;
+  for (int k = 0; k < v.d; ++k) {
+    q[k] = c[k] + (oo % 3) - 1;
+    oo /= 3;
+  }
+  if (!in_grid(q, v.d, v.n)) return;
+  int qb = morton_key(q, v.d, v.l);
+  if (qb >= b) return;
+  const int mb = start[b + 1] - start[b], mq = start[qb + 1] - start[qb];
+  copy_transposed(v.xx(qb, slot5(q, c, v.d)), v.M, v.xx(b, slot5(c, q, v.d)), v.M, mb, mq);
+}
+
+// M2L blocks A_bd = A(t^{b,i}, t^{d,i}) for d in IL(b) with b < d (the rest:
+// k_setup_m2l_mirror); grid (nb, ns6)
 __global__ void k_setup_m2l(LV v, const int* __restrict__ pivpos, int nR, KParams kp, Pts P) {
   int b = blockIdx.x, s = blockIdx.y;
   int c[3], q[3];
@@ -99,6 +148,7 @@ __global__ void k_setup_m2l(LV v, const int* __restrict__ pivpos, int nR, KParam
   slot6_coords(c, s, v.d, q);
   if (!in_grid(q, v.d, v.n) || cheb(c, q, v.d) <= 1) return;
   int qb = morton_key(q, v.d, v.l);
+  if (qb < b) return;
   int rb = v.r[b], rq = v.r[qb];
   double* A = v.ly(b, s);
   const int* tb = pivpos + (size_t)b * nR;
@@ -107,6 +157,18 @@ __global__ void k_setup_m2l(LV v, const int* __restrict__ pivpos, int nR, KParam
     int i = e % rb, j = e / rb;
     A[i + (size_t)j * v.R] = keval(kp, P, tb[i], tq[j]);
   }
+}
+
+// A_bd = A_db^T for d in IL(b), d < b; grid (nb, ns6)
+__global__ void k_setup_m2l_mirror(LV v) {
+  int b = blockIdx.x, s = blockIdx.y;
+  int c[3], q[3];
+  morton_coords(b, v.d, v.l, c);
+  slot6_coords(c, s, v.d, q);
+  if (!in_grid(q, v.d, v.n) || cheb(c, q, v.d) <= 1) return;
+  int qb = morton_key(q, v.d, v.l);
+  if (qb >= b) return;
+  copy_transposed(v.ly(qb, slot6(q, c, v.d)), v.R, v.ly(b, s), v.R, v.r[b], v.r[qb]);
 }
 
 // U^dag_b / V^dag_b (level l >= 3): rows of the parent's NNCA basis that belong
@@ -1559,6 +1621,7 @@ static int setup_level(Handle& h, int l) {
   const int n3 = ipow(3, d);
   if (l == L) {
     k_setup_leaf_K<<<dim3(F.nb, n3), 256, 0, st>>>(v, h.start + h.soff[L], h.kp, h.P()); ++h.nlaunch;
+    k_setup_leaf_K_mirror<<<dim3(F.nb, n3), 256, 0, st>>>(v, h.start + h.soff[L]); ++h.nlaunch;
     k_copy_basis<<<F.nb, 256, 0, st>>>(v, N.U, N.M, N.R); ++h.nlaunch;
   } else {
     FacLevel& C = h.fac[l + 1];
@@ -1566,6 +1629,7 @@ static int setup_level(Handle& h, int l) {
     k_setup_parent<<<dim3(F.nb, n3), 256, 0, st>>>(v, vc, C.xoff); ++h.nlaunch;
   }
   k_setup_m2l<<<dim3(F.nb, F.ns6), 128, 0, st>>>(v, N.pivpos, N.R, h.kp, h.P()); ++h.nlaunch;
+  k_setup_m2l_mirror<<<dim3(F.nb, F.ns6), 256, 0, st>>>(v); ++h.nlaunch;
   if (l >= 3) {
     const NnLevel& Np = h.nn[l - 1];
     k_setup_udag<<<F.nb, 128, 0, st>>>(v, Np.U, Np.M, Np.R, Np.rank, N.rank); ++h.nlaunch;
@@ -1648,6 +1712,188 @@ static void collect_group_times(Handle& h) {
     cudaEventDestroy(e.second.second);
   }
   h.g_ev.clear();
+}
+
+// The register-resident LU panel (k_lu_panel_rg) spread over a thread-block
+// cluster of CS CTAs per item, for panels taller than one CTA holds in
+// registers (the top system): the FP64 rank-1 updates, which bound such a
+// panel on one SM (about two FP64 FMAs per clock per SM), run on CS SMs.
+// Measured at 65,536 points: the top system's LU 3.1 -> 2.7 ms against the
+// shared-memory panel, but slower than k_lu_panel_rg on panels of up to 512 rows (the
+// cluster barrier and the distributed-shared-memory reads cost more per
+// column than the FP64 work they spread), so those keep one CTA.
+// CTA rank r holds panel rows r * blockDim.x ..., one per thread.  Per
+// column, each warp publishes its best candidate (key, position, row and
+// pivot reciprocal) in its CTA's double-buffered slots; one cluster barrier;
+// then every warp reads all CS x warps candidates through distributed
+// shared memory (lane k: candidates k and k + 32), keeps the best (largest
+// key, then smallest position) and takes the winning row from its owner's
+// slot.  The same operations per entry as k_lu_panel_rg, so the same
+// results.  Control flow is uniform over the cluster (the item, and every
+// decision, is the same in all its CTAs), and a cluster barrier precedes
+// every exit, so no CTA leaves while another may read its shared memory.
+// grid (items x CS), cluster CS, blockDim a multiple of 32 with CS x warps <= 64.
+constexpr int LU_CL_MAXT = 256;
+__global__ void __launch_bounds__(LU_CL_MAXT) k_lu_panel_cl(const LuItem* items, int k0, int* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+  __shared__ long long ck[2][LU_CL_MAXT / 32];
+  __shared__ int cp[2][LU_CL_MAXT / 32];
+  __shared__ double crow[2][LU_CL_MAXT / 32][LU_NB + 1];
+  __shared__ long long thr[LU_NB];
+  const LuItem it = items[blockIdx.x / CS];
+  const int n = it.n;
+  if (k0 >= n) return;   // the whole cluster: same item
+  const int h = n - k0;
+  const int nbw = min(LU_NB, h);
+  const int t = cr * blockDim.x + threadIdx.x;   // panel row of this thread
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ncand = CS * nw;
+  double* A = it.a;
+  const int ld = it.ld;
+  double a[LU_NB];
+#pragma unroll
+  for (int j = 0; j < LU_NB; ++j) a[j] = (t < h && j < nbw) ? A[(k0 + t) + (size_t)(k0 + j) * ld] : 0.0;
+  if (threadIdx.x < LU_NB)
+    thr[threadIdx.x] =
+        __double_as_longlong(1e-14 * ((it.colmax && (int)threadIdx.x < nbw) ? it.colmax[k0 + threadIdx.x] : 0.0));
+  int pos = t;
+  bool live = t < h;
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < LU_NB; ++jj) {
+    if (jj < nbw) {
+      const int par = jj & 1;
+      long long key = -1;
+      if (live) {
+        const long long kb = __double_as_longlong(fabs(a[jj]));
+        key = kb > 0x7ff0000000000000LL ? -1 : kb;
+      }
+      long long wk = key;
+      int wp = pos;
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, wk, o);
+        const int op = __shfl_xor_sync(0xffffffffu, wp, o);
+        if (ok > wk || (ok == wk && op < wp)) {
+          wk = ok;
+          wp = op;
+        }
+      }
+      if (wk >= 0 && pos == wp) {
+        double* cw = crow[par][w];
+#pragma unroll
+        for (int cc = 0; cc < LU_NB; ++cc)
+          if (cc >= jj) cw[cc] = a[cc];
+        cw[LU_NB] = 1.0 / a[jj];
+      }
+      if (lane == 0) {
+        ck[par][w] = wk;
+        cp[par][w] = wp;
+      }
+      cl.sync();
+      long long bk = -1;
+      int bp = 0x7fffffff, bs = 0;
+      for (int k = lane; k < ncand; k += 32) {
+        const int r = k / nw, u = k % nw;
+        const long long k2 = *cl.map_shared_rank(&ck[par][u], r);
+        const int p2 = *cl.map_shared_rank(&cp[par][u], r);
+        if (k2 > bk || (k2 == bk && p2 < bp)) {
+          bk = k2;
+          bp = p2;
+          bs = k;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (ok > bk || (ok == bk && op < bp)) {
+          bk = ok;
+          bp = op;
+          bs = os;
+        }
+      }
+      if (!(bk > thr[jj]) || !(bk >= 0x0010000000000000LL)) {
+        if (cr == 0) {
+          for (int q = jj + (int)threadIdx.x; q < nbw; q += blockDim.x) it.ipiv[k0 + q] = k0 + q;
+          if (threadIdx.x == 0) set_err(err, DERR_SINGULAR);
+        }
+        cl.sync();
+        return;
+      }
+      const double* pr = cl.map_shared_rank(&crow[par][bs % nw][0], bs / nw);
+      const double prl = pr[lane];
+      const double rp = pr[LU_NB];
+      if (live && pos == bp) {
+        it.ipiv[k0 + jj] = k0 + bp;
+        live = false;
+        pos = jj;
+      } else if (pos == jj) {
+        pos = bp;
+      }
+      const double l = live ? a[jj] * rp : 0.0;
+      if (live) a[jj] = l;
+#pragma unroll
+      for (int cc = 0; cc < LU_NB; ++cc)
+        if (cc > jj && cc < nbw) {
+          const double pc = __shfl_sync(0xffffffffu, prl, cc);
+          if (live) a[cc] -= l * pc;
+        }
+    }
+  }
+  cl.sync();   // the last column's slots may still be read by the other CTAs
+  if (t < h)
+#pragma unroll
+    for (int j = 0; j < LU_NB; ++j)
+      if (j < nbw) A[(k0 + pos) + (size_t)(k0 + j) * ld] = a[j];
+}
+
+// CTAs per cluster for the panels of `cnt` items of up to `hc` rows, or 1 for
+// one CTA per item: at most LU_CL_MAXT rows per CTA; more CTAs while the
+// launch leaves SMs idle and each CTA keeps at least 64 rows
+static int lu_panel_cluster(int cnt, int hc, int nsm) {
+  int cs = 1;
+  while (cs < 8 && (hc + cs - 1) / cs > LU_CL_MAXT) cs *= 2;
+  while (cs < 8 && cnt * cs * 2 <= nsm && (hc + 2 * cs - 1) / (2 * cs) >= 64) cs *= 2;
+  return cs;
+}
+
+// the LU panel of `cnt` items at column k0 (rows up to hc = capacity - k0):
+// one CTA with the rows in registers, a cluster per item for taller panels,
+// or the shared-memory / global-memory panels
+static int lu_panel(Handle& h, const LuItem* items, int cnt, int k0, int hc) {
+  cudaStream_t st = h.stream;
+  const int cs = lu_panel_cluster(cnt, hc, h.nsm);
+  if (hc <= LU_RG_MAXH) {
+    k_lu_panel_rg<<<cnt, (hc + 31) / 32 * 32, 0, st>>>(items, k0, h.derr);
+    ++h.nlaunch;
+  } else if (cs > 1 && (hc + cs - 1) / cs <= LU_CL_MAXT && hc <= h.panel_rows) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cnt * cs);
+    cfg.blockDim = dim3(((hc + cs - 1) / cs + 31) / 32 * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    AIFMM_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_lu_panel_cl, items, k0, h.derr));
+    ++h.nlaunch;
+  } else {
+    const int hh = std::min(hc, h.panel_rows);
+    k_lu_panel_sm<<<cnt, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(items, k0, h.panel_rows,
+                                                                                          h.derr);
+    ++h.nlaunch;
+    if (hc > h.panel_rows) {
+      k_lu_panel_big<<<cnt, 256, 0, st>>>(items, k0, h.panel_rows, h.derr);
+      ++h.nlaunch;
+    }
+  }
+  return HOK;
 }
 
 // k_cmp_qrcp for c.cnt boxes (nsides each) in clusters of q CTAs; few
@@ -1872,19 +2118,8 @@ static int factor_level(Handle& h, int l) {
       const int ctot = F.P + e.ncmax;
       const int tiles = (F.P + 63) / 64, ctiles = tiles + (e.ncmax + 63) / 64;
       for (int k0 = 0; k0 < F.P; k0 += LU_NB) {
-        const int hh = std::min(F.P - k0, maxh);
         dp.begin("lu_panel");
-        if (F.P - k0 <= LU_RG_MAXH) {
-          k_lu_panel_rg<<<cnt, (F.P - k0 + 31) / 32 * 32, 0, st>>>(e.lu, k0, h.derr);
-          ++h.nlaunch;
-        } else {
-          k_lu_panel_sm<<<cnt, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(e.lu, k0, maxh,
-                                                                                                h.derr);
-          ++h.nlaunch;
-          if (F.P - k0 > maxh) {
-            k_lu_panel_big<<<cnt, 256, 0, st>>>(e.lu, k0, maxh, h.derr); ++h.nlaunch;
-          }
-        }
+        if (int rc = lu_panel(h, e.lu, cnt, k0, F.P - k0)) return rc;
         dp.end();
         dp.begin("lu_laswp");
         k_lu_laswp<<<dim3((ctot + 127) / 128, cnt), 128, 0, st>>>(e.lu, k0, maxh); ++h.nlaunch;
@@ -2074,11 +2309,19 @@ int run_factor(Handle& h) {
     AIFMM_CUDA_TRY(h, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h.device));
     h.l2_bytes = (size_t)l2;
   }
+  DetailProf dpf;   // diagnostic: level set-up, whole level, top LU
+  dpf.on = std::getenv("AIFMM_PROFILE_DETAIL") != nullptr;
+  dpf.st = st;
   for (int l = L; l >= 2; --l) {
+    dpf.begin("setup");
     int e = setup_level(h, l);
     if (e) return e;
+    dpf.end();
+    dpf.begin("level_total");
     e = factor_level(h, l);
     if (e) return e;
+    dpf.end();
+    dpf.report(l);
     collect_group_times(h);
     double fc[2] = {0.0, 0.0};
     AIFMM_CUDA_TRY(h, cudaMemcpy(fc, h.dacc, 2 * sizeof(double), cudaMemcpyDeviceToHost));
@@ -2097,6 +2340,7 @@ int run_factor(Handle& h) {
   h.top = hnew<double>(h, (size_t)nt * nt);
   h.top_ipiv = hnew<int>(h, nt);
   h.top_perm = hnew<int>(h, nt, false);
+  dpf.begin("top_lu");
   int* toff = hnew<int>(h, F2.nb + 1, false);
   double* cm = hnew<double>(h, nt);
   LuItem* it = hnew<LuItem>(h, 1, false);
@@ -2116,24 +2360,15 @@ int run_factor(Handle& h) {
   AIFMM_CUDA_TRY(h, cudaMemcpyAsync(it, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
   k_colmax<<<1, 256, 0, st>>>(it, cm, nt); ++h.nlaunch;
   for (int k0 = 0; k0 < h.ntop; k0 += LU_NB) {
-    const int hh = std::min(h.ntop - k0, h.panel_rows);
-    if (h.ntop - k0 <= LU_RG_MAXH) {
-      k_lu_panel_rg<<<1, (h.ntop - k0 + 31) / 32 * 32, 0, st>>>(it, k0, h.derr);
-      ++h.nlaunch;
-    } else {
-      k_lu_panel_sm<<<1, lu_panel_threads(hh), sizeof(double) * (size_t)hh * LU_NB, st>>>(it, k0, h.panel_rows,
-                                                                                             h.derr);
-      ++h.nlaunch;
-      if (h.ntop - k0 > h.panel_rows) {
-        k_lu_panel_big<<<1, 256, 0, st>>>(it, k0, h.panel_rows, h.derr); ++h.nlaunch;
-      }
-    }
+    if (int rc = lu_panel(h, it, 1, k0, h.ntop - k0)) return rc;
     k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
     k_lu_trsm<<<dim3((h.ntop + 3) / 4, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
     k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
   }
   k_ipiv_perm<<<1, 1, 0, st>>>(h.top_ipiv, h.ntop, h.top_perm); ++h.nlaunch;
+  dpf.end();
+  dpf.report(1);
   h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;
   AIFMM_CUDA_TRY(h, cudaGetLastError());
   AIFMM_CUDA_TRY(h, cudaStreamSynchronize(st));
