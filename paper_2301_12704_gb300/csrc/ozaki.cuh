@@ -240,8 +240,8 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
       // ---- MMAs: digit-pair weights s + t = 0..4 each in its own
       // accumulator (exact: at most 5 pairs x 32 of K x 2^14 < 2^22 per
       // weight), 5..8 together in FP32; recombined once per chunk, the exact
-      // part as a 64-bit integer in units of 2^-28, then scaled by the row
-      // and column exponents in FP64
+      // part as a 64-bit integer in units of 2^-28 joined with the FP32 part
+      // in units of 2^-40, then scaled by the row and column exponents in FP64
       float acc[6][2][4];
 #pragma unroll
       for (int x = 0; x < 6; ++x)
@@ -289,11 +289,18 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
             wgt *= 128.0f;
           }
           const int i = wr + g + 8 * (q >> 1), jl = wc + 8 * b + 2 * cq + (q & 1);
-          const double sum = fma((double)tt, 0x1p-28, (double)acc[5][b][q]);
-          // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
+          // the exact part (units of 2^-28, |tt| < 2^48) and the FP32 part
+          // (|acc5| < 2^-13) as one integer in units of 2^-40 (|X| < 2^60):
+          // one conversion and one FP64 FMA per output and chunk, the FP64
+          // pipe being the tile's bottleneck on parts with a narrow one
+          const long long X = tt * 4096 + (long long)__float2int_rn(acc[5][b][q] * 0x1p40f);
+          const double xd = (double)X;
+          // scale 2^(E_i - 1029) 2^(E_j - 1029) 2^-40 as a biased exponent
           const int be = ea[i] + eb[jl] - 2058 + 1023;
-          const double sc = be > 0 && be < 2047 ? __longlong_as_double((long long)be << 52) : 0.0;
-          acc64[b][q] = fma(sum, sc, acc64[b][q]);
+          if (be > 40 && be < 2047)
+            acc64[b][q] = fma(xd, __longlong_as_double((long long)(be - 40) << 52), acc64[b][q]);
+          else if (be > 0 && be < 2047)   // 2^(be - 40) below the normal range: in two steps
+            acc64[b][q] = fma(xd * 0x1p-40, __longlong_as_double((long long)be << 52), acc64[b][q]);
         }
       __syncthreads();   // the next chunk overwrites the planes and exponents
     }
