@@ -90,9 +90,9 @@ int dgemm_tc(const double* A, int64_t lda, const double* B, int64_t ldb, double*
       ldb > INT32_MAX || ldc > INT32_MAX)
     return 1;
   if (m == 0 || n == 0) return 0;
-  if (!raise_smem_once((const void*)k_gemm_oz<KB, S>, oz_smem(S), KB ? 2 : 1)) return 6;
+  if (!raise_smem_once((const void*)k_gemm_oz<KB, S>, oz_smem(S, KB), KB ? 2 : 1)) return 6;
   dim3 grid((n + 63) / 64, (m + 63) / 64);
-  k_gemm_oz<KB, S><<<grid, 256, oz_smem(S), (cudaStream_t)stream>>>(A, lda, B, ldb, C, ldc, m, n, k, alpha);
+  k_gemm_oz<KB, S><<<grid, 256, oz_smem(S, KB), (cudaStream_t)stream>>>(A, lda, B, ldb, C, ldc, m, n, k, alpha);
   if (cudaGetLastError() != cudaSuccess) return 6;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return 6;
   return 0;

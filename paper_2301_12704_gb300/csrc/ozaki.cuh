@@ -44,11 +44,16 @@ namespace aifmm {
 constexpr int OZ_S = 7;                // digits per operand
 constexpr int OZ_KC = 32;              // K chunk
 constexpr int OZ_LD = OZ_KC + 8;       // padded smem row (bf16 elements, 20 words): conflict-free fragment loads
-// bytes of dynamic shared memory of the tile with S digits per operand
-constexpr int oz_smem(int S) { return S * (64 + 32) * OZ_LD * 2 + 3 * 64 * 4; }
-constexpr int OZ_SMEM = oz_smem(OZ_S);
+// bytes of dynamic shared memory of the tile with S digits per operand: the
+// balanced variant (KB) stages A and one 32-column half of B per chunk; the
+// other stages A and both halves, and parks half 1's FP64 results (8 doubles
+// per thread)
+constexpr int oz_smem(int S, bool KB) {
+  return KB ? S * (64 + 32) * OZ_LD * 2 + 3 * 64 * 4 : S * (64 + 64) * OZ_LD * 2 + 3 * 64 * 4 + 8 * 256 * 8;
+}
+constexpr int OZ_SMEM = oz_smem(OZ_S, false);
 constexpr int OZ_S8 = 8;               // digits of the high-precision variant
-constexpr int OZ_SMEM8 = oz_smem(OZ_S8);
+constexpr int OZ_SMEM8 = oz_smem(OZ_S8, true);
 constexpr int OZ_NEG = -(1 << 20);     // exponent of an all-zero row or column (balanced contraction)
 
 // biased exponent of |x| (0 for zero and denormals, which are flushed)
@@ -92,6 +97,28 @@ __device__ inline void oz_digits(double x, int E, __nv_bfloat16* out, int stride
   for (int s = 0; s < S; ++s) out[s * stride] = __ushort_as_bfloat16(d[s]);
 }
 
+// one chunk's digit-pair sums of an output into its FP64 result: weights
+// 0..4 exact (acc[0..4]), 5.. in FP32 (acc[5]); the exact part as a 64-bit
+// integer in units of 2^-28 (|tt| < 2^48) joined with the FP32 part
+// (|acc5| < 2^-13) in units of 2^-40 (|X| < 2^60), converted once and added
+// with one FMA scaled by 2^(be - 1023 - 40), be the biased exponent of the
+// chunk's row and column scales
+__device__ inline void oz_recombine(const float* acc, int stride, int be, double& out) {
+  long long tt = 0;
+  float wgt = 1.0f;
+#pragma unroll
+  for (int x = 0; x < 5; ++x) {
+    tt += (long long)__float2int_rn(acc[x * stride] * wgt) * (1ll << (7 * (4 - x)));
+    wgt *= 128.0f;
+  }
+  const long long X = tt * 4096 + (long long)__float2int_rn(acc[5 * stride] * 0x1p40f);
+  const double xd = (double)X;
+  if (be > 40 && be < 2047)
+    out = fma(xd, __longlong_as_double((long long)(be - 40) << 52), out);
+  else if (be > 0 && be < 2047)   // 2^(be - 40) below the normal range: in two steps
+    out = fma(xd * 0x1p-40, __longlong_as_double((long long)be << 52), out);
+}
+
 __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -102,7 +129,7 @@ __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
 
 // C[0..mr, 0..nc] += alpha * op(A)[0..mr, 0..K) B[0..K, 0..nc]; op(A) = A
 // column-major (lda) or, with TA, A^T for A column-major K x mr (lda);
-// B column-major (ldb), C column-major (ldc).  smem: oz_smem(S) bytes.
+// B column-major (ldb), C column-major (ldc).  smem: oz_smem(S, KB) bytes.
 //
 // S: digits per operand (7, or 8 for 56-bit slices; pairs with s + t <= S + 1
 // are multiplied: 39 or 49 MMAs per 16-deep step).  KB (balanced
@@ -122,9 +149,178 @@ __device__ inline void oz_mma(float* c, const uint32_t* a, const uint32_t* b) {
 // accumulators and FP64 results are live, so a thread needs at most 128
 // registers and a CTA 54 KB (S = 7) or 62 KB (S = 8) of shared memory: two
 // CTAs share an SM and hide each other's staging and MMA latencies.
+// The tile without the balanced contraction: A's digits do not depend on the
+// half of B, so each chunk stages A's digit planes once and B's for all 64
+// columns, then runs both halves' MMAs; half 0's FP64 results stay in
+// registers and half 1's are parked in shared memory (8 doubles per thread),
+// so the register budget of the two-CTA-per-SM tile holds.  Every output
+// sees the same digits, chunk sums and recombinations as in the one-half-
+// at-a-time form.  smem: oz_smem(S, false) bytes.
+template <bool TA, int S>
+__device__ inline void tile_gemm_64_oz_sa(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                                          int mr, int nc, int K, double alpha, unsigned char* smem) {
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [S][64][OZ_LD] (row, k)
+  __nv_bfloat16* Bs = As + S * 64 * OZ_LD;                               // [S][64][OZ_LD] (column, k)
+  int* ea = reinterpret_cast<int*>(Bs + S * 64 * OZ_LD);                 // [64] row exponents
+  int* eb = ea + 64;                                                     // [64] column exponents
+  double* park = reinterpret_cast<double*>(eb + 128);                    // [8][256] half 1's results
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int g = lane >> 2, cq = lane & 3;
+  const int wr = 16 * (w & 3);                                           // warp's rows
+  const int wc = 16 * (w >> 2);                                          // warp's columns in a half
+  const int nh = nc > 32 ? 2 : 1;                                        // halves with columns
+  double acc64[2][4];                                                    // half 0 [n8 block][fragment]
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc64[b][q] = 0.0;
+#pragma unroll
+  for (int x = 0; x < 8; ++x) park[x * 256 + tid] = 0.0;   // each thread its own entries
+  for (int k0 = 0; k0 < K; k0 += OZ_KC) {
+    const int kc = min(OZ_KC, K - k0);
+    if (tid < 128) (tid < 64 ? ea : eb)[tid & 63] = 0;
+    __syncthreads();
+    // B: warp w takes the columns 4w..4w+3 of each half, lane the k
+    double bv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = 32 * (q >> 2) + 4 * w + (q & 3);
+      bv[q] = (j < nc && lane < kc) ? B[(k0 + lane) + (size_t)j * ldb] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int bm = oz_bexp(bv[q]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      if (lane == 0) eb[32 * (q >> 2) + 4 * w + (q & 3)] = bm;
+    }
+    // A: as in tile_gemm_64_oz
+    double av[8];
+    if (!TA) {
+      const int i = lane + 32 * (w >> 2), kb0 = 8 * (w & 3);
+      int am = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = kb0 + q;
+        const double x = (i < mr && k < kc) ? A[i + (size_t)(k0 + k) * lda] : 0.0;
+        av[q] = x;
+        am = max(am, oz_bexp(x));
+      }
+      atomicMax(&ea[i], am);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = 8 * w + q;
+        const double x = (i < mr && lane < kc) ? A[(k0 + lane) + (size_t)i * lda] : 0.0;
+        av[q] = x;
+        int am = oz_bexp(x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+        if (lane == 0) ea[i] = am;
+      }
+    }
+    __syncthreads();
+    // ---- digits into shared memory
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int jl = 32 * (q >> 2) + 4 * w + (q & 3);
+      oz_digits<S>(bv[q], eb[jl], Bs + jl * OZ_LD + lane, 64 * OZ_LD);
+    }
+    if (TA) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = 8 * w + q;
+        oz_digits<S>(av[q], ea[i], As + i * OZ_LD + lane, 64 * OZ_LD);
+      }
+    } else {
+      const int i = lane + 32 * (w >> 2), kb0 = 8 * (w & 3);
+      uint32_t pk[S][4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint16_t d[S];
+        oz_digit_bits<S>(av[q], ea[i], d);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) {
+          if (q & 1) pk[s2][q >> 1] |= (uint32_t)d[s2] << 16;
+          else pk[s2][q >> 1] = d[s2];
+        }
+      }
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2)
+        *reinterpret_cast<uint4*>(As + s2 * 64 * OZ_LD + i * OZ_LD + kb0) =
+            make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+    }
+    __syncthreads();
+    for (int hc = 0; hc < nh; ++hc) {
+      float acc[6][2][4];
+#pragma unroll
+      for (int x = 0; x < 6; ++x)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[x][b][q] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < OZ_KC; kk += 16) {
+        uint32_t bf[S][2][2];
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const __nv_bfloat16* base = Bs + t * 64 * OZ_LD + (32 * hc + wc + 8 * b + g) * OZ_LD + kk + 2 * cq;
+            bf[t][b][0] = *reinterpret_cast<const uint32_t*>(base);
+            bf[t][b][1] = *reinterpret_cast<const uint32_t*>(base + 8);
+          }
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) {
+          uint32_t af[4];
+          const __nv_bfloat16* base = As + s2 * 64 * OZ_LD + (wr + g) * OZ_LD + kk + 2 * cq;
+          af[0] = *reinterpret_cast<const uint32_t*>(base);
+          af[1] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD);
+          af[2] = *reinterpret_cast<const uint32_t*>(base + 8);
+          af[3] = *reinterpret_cast<const uint32_t*>(base + 8 * OZ_LD + 8);
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            if (s2 + t > S + 1) continue;        // s + t > S + 1: dropped
+            const int grp = min(s2 + t, 5);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) oz_mma(acc[grp][b], af, bf[t][b]);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = wr + g + 8 * (q >> 1), jl = 32 * hc + wc + 8 * b + 2 * cq + (q & 1);
+          const int be = ea[i] + eb[jl] - 2058 + 1023;
+          if (hc == 0) {
+            oz_recombine(&acc[0][b][q], 8, be, acc64[b][q]);
+          } else {
+            double p = park[(b * 4 + q) * 256 + tid];
+            oz_recombine(&acc[0][b][q], 8, be, p);
+            park[(b * 4 + q) * 256 + tid] = p;
+          }
+        }
+    }
+    __syncthreads();   // the next chunk overwrites the planes and exponents
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = wr + g + 8 * (q >> 1), j = wc + 8 * b + 2 * cq + (q & 1);
+      if (i < mr && j < nc) C[i + (size_t)j * ldc] += alpha * acc64[b][q];
+      if (nh > 1 && i < mr && j + 32 < nc) C[i + (size_t)(j + 32) * ldc] += alpha * park[(b * 4 + q) * 256 + tid];
+    }
+}
+
 template <bool TA = false, bool KB = false, int S = OZ_S>
 __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                                        int mr, int nc, int K, double alpha, unsigned char* smem) {
+  if (!KB) {
+    tile_gemm_64_oz_sa<TA, S>(A, lda, B, ldb, C, ldc, mr, nc, K, alpha, smem);
+    return;
+  }
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);            // [S][64][OZ_LD] (row, k)
   __nv_bfloat16* Bs = As + S * 64 * OZ_LD;                               // [S][32][OZ_LD] (column of the half, k)
   int* ea = reinterpret_cast<int*>(Bs + S * 32 * OZ_LD);                 // [64] row exponents
@@ -281,26 +477,9 @@ __device__ inline void tile_gemm_64_oz(const double* A, int lda, const double* B
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          long long tt = 0;
-          float wgt = 1.0f;
-#pragma unroll
-          for (int x = 0; x < 5; ++x) {
-            tt += (long long)__float2int_rn(acc[x][b][q] * wgt) * (1ll << (7 * (4 - x)));
-            wgt *= 128.0f;
-          }
           const int i = wr + g + 8 * (q >> 1), jl = wc + 8 * b + 2 * cq + (q & 1);
-          // the exact part (units of 2^-28, |tt| < 2^48) and the FP32 part
-          // (|acc5| < 2^-13) as one integer in units of 2^-40 (|X| < 2^60):
-          // one conversion and one FP64 FMA per output and chunk, the FP64
-          // pipe being the tile's bottleneck on parts with a narrow one
-          const long long X = tt * 4096 + (long long)__float2int_rn(acc[5][b][q] * 0x1p40f);
-          const double xd = (double)X;
-          // scale 2^(E_i - 1029) 2^(E_j - 1029) 2^-40 as a biased exponent
-          const int be = ea[i] + eb[jl] - 2058 + 1023;
-          if (be > 40 && be < 2047)
-            acc64[b][q] = fma(xd, __longlong_as_double((long long)(be - 40) << 52), acc64[b][q]);
-          else if (be > 0 && be < 2047)   // 2^(be - 40) below the normal range: in two steps
-            acc64[b][q] = fma(xd * 0x1p-40, __longlong_as_double((long long)be << 52), acc64[b][q]);
+          // scale 2^(E_i - 1029) 2^(E_j - 1029) as a biased exponent
+          oz_recombine(&acc[0][b][q], 8, ea[i] + eb[jl] - 2058 + 1023, acc64[b][q]);
         }
       __syncthreads();   // the next chunk overwrites the planes and exponents
     }
