@@ -2364,7 +2364,13 @@ int run_factor(Handle& h) {
     k_lu_laswp<<<dim3((h.ntop + 127) / 128, 1), 128, 0, st>>>(it, k0, h.panel_rows); ++h.nlaunch;
     k_lu_trsm<<<dim3((h.ntop + 3) / 4, 1), 128, 0, st>>>(it, k0); ++h.nlaunch;
     int tiles = (h.ntop + 63) / 64;
-    k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0); ++h.nlaunch;
+    // trailing updates on the 8-digit tensor-core tile, as in the levels'
+    // pivot LUs (FP64 FMAs in the FP32 / FP64-FMA product modes)
+    if (product_mode(h) == PM_OZ)
+      k_lu_gemm<PM_OZ8><<<dim3(tiles, tiles, 1), 256, OZ_SMEM8, st>>>(it, k0);
+    else
+      k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0);
+    ++h.nlaunch;
   }
   k_ipiv_perm<<<1, 1, 0, st>>>(h.top_ipiv, h.ntop, h.top_perm); ++h.nlaunch;
   dpf.end();
