@@ -34,6 +34,7 @@ UNIT = "points/s"
 # Digit-pair BF16 MMAs per FP64 multiply-add of the 7-digit tensor-core tile
 # (pairs of digits s + t <= 8 of seven 7-bit digits per operand).
 OZ_PAIRS = 39
+TRAFFIC_65536 = {"k_schur": 1.157e8, "k_cmp_qrcp": 1.137e7}
 # Roofline denominators when MEASURED_PEAKS.json is absent: the profiling
 # recipe's fallback (one earlier GB300 measurement).
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -440,12 +441,18 @@ def main():
     # block sizes
     names = ["compress_other", "pivot_lu", "z_solve", "schur", "qrcp"]
     G_SCHUR, G_QRCP = 3, 4
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum,
+    # averaged over one factorisation's launches) from one ncu capture of
+    # these kernels as they now stand, at the 65,536-point workload (summary
+    # under profiles/); unknown (None) for other sizes
+    traffic = TRAFFIC_65536 if args.n == 65536 else {}
 
     def kernel_roof(g):
         ms, fl, nl = groups_ms[g], groups_fl[g], groups_n[g]
         fp64 = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
         base = {"launches": nl, "avg_launch_ms": ms / max(1, nl), "share_of_factor": ms / max(1e-9, tf),
-                "flops_per_launch": fl / max(1, nl), "traffic": None}
+                "flops_per_launch": fl / max(1, nl),
+                "traffic": traffic.get("k_cmp_qrcp" if g == G_QRCP else "k_schur")}
         if g == G_QRCP:
             base.update({"kernel": "k_cmp_qrcp", "bound": "alu", "achieved": fp64, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": fp64 / fp64_peak if fp64_peak else None,
