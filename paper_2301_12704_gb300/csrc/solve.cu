@@ -117,7 +117,9 @@ __global__ void k_fwd_prep(LV v, SV s, int col, SolveItem* items) {
 // forward sweep, step 2: right-hand-side Schur operations on the coupled
 // rows: X_p -= K_pb w_x (p not yet eliminated), Lc_p -= P2L_pb w_x
 // (p eliminated), Lc_b += w_z.  grid (3^d * rt, column tiles, cnt), 64-row
-// tiles of the target block
+// tiles of the target block.  PM: the products' mode (PM_FMA, or the
+// 8-digit balanced tensor-core tile for many right-hand sides)
+template <int PM>
 __global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col, int rt) {
   int t = blockIdx.z, o = blockIdx.x / rt, ti = blockIdx.x % rt;
   int b = colour_box(col, t, v.d, v.l);
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) k_fwd_upd(LV v, SV s, int col, int rt) {
     ldt = v.M;
   }
   if (i0 >= rows) return;
-  tile_gemm_64(A + i0, lda, w + (size_t)j0 * v.P, v.P, tp + i0 + (size_t)j0 * ldt, ldt, min(64, rows - i0), nc, m,
+  tile_gemm<PM>(A + i0, lda, w + (size_t)j0 * v.P, v.P, tp + i0 + (size_t)j0 * ldt, ldt, min(64, rows - i0), nc, m,
                -1.0);
 }
 
@@ -298,6 +300,7 @@ __device__ inline bool bwd_term(const LV& v, const SV& s, int col, const YSrc& y
 // side; k_bwd_sum then takes w_x += (-1) P_o over the neighbours in order
 // and clears Pb for the next colour.
 // Pb: [cnt][3^d][M x nrhs], ld M.  grid (row tiles * 3^d, column tiles, cnt)
+template <int PM>
 __global__ void __launch_bounds__(256) k_bwd_part(LV v, SV s, int col, YSrc y, int mt, double* __restrict__ Pb) {
   int t = blockIdx.z;
   int b = colour_box(col, t, v.d, v.l);
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(256) k_bwd_part(LV v, SV s, int col, YSrc y, i
   if (!bwd_term(v, s, col, y, b, o, A, B, ldb, cols)) return;
   const int n3 = ipow(3, v.d);
   double* P = Pb + ((size_t)t * n3 + o) * v.M * s.nrhs;
-  tile_gemm_64(A + i0, v.M, B + (size_t)j0 * ldb, ldb, P + i0 + (size_t)j0 * v.M, v.M, min(64, m - i0),
+  tile_gemm<PM>(A + i0, v.M, B + (size_t)j0 * ldb, ldb, P + i0 + (size_t)j0 * v.M, v.M, min(64, m - i0),
                min(64, s.nrhs - j0), cols, 1.0);
 }
 
@@ -502,6 +505,11 @@ constexpr int MAX_GATHER = 27 * 1024;   // rows; 216 KB of shared memory
 // one-launch solve (k_lus_small); larger ones the blocked multi-launch solve
 constexpr int LS_MAXN = 1024;
 
+// products of the solve sweeps: the 8-digit balanced tensor-core tile for
+// more right-hand sides than the narrow FP64 form takes, in the default
+// (FP64-precision tensor-core) product mode; FP64 FMAs otherwise
+static bool solve_tc(const Handle& h, int ncols) { return !h.tf32 && !h.fp32 && !h.fma_gemm && ncols > THIN_NC; }
+
 static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int ncols, int swap, cudaStream_t st) {
   if (P <= LS_MAXN && ncols <= 4 && swap != 2) {
     const int nc = ncols <= 1 ? 1 : ncols <= 2 ? 2 : 4;
@@ -528,7 +536,12 @@ static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int nco
     }
     ++h.nlaunch;
     if (k0 + TB < P) {
-      k_lus_update<1><<<dim3(ctiles, (P - k0 - TB + 63) / 64, cnt), 256, 0, st>>>(items, k0); ++h.nlaunch;
+      const dim3 g(ctiles, (P - k0 - TB + 63) / 64, cnt);
+      if (solve_tc(h, ncols))
+        k_lus_update<1, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(items, k0);
+      else
+        k_lus_update<1><<<g, 256, 0, st>>>(items, k0);
+      ++h.nlaunch;
     }
   }
   for (int k0 = ((P - 1) / TB) * TB; k0 >= 0; k0 -= TB) {
@@ -539,7 +552,12 @@ static void lus_apply(Handle& h, const SolveItem* items, int cnt, int P, int nco
     }
     ++h.nlaunch;
     if (k0 > 0) {
-      k_lus_update<0><<<dim3(ctiles, (k0 + 63) / 64, cnt), 256, 0, st>>>(items, k0); ++h.nlaunch;
+      const dim3 g(ctiles, (k0 + 63) / 64, cnt);
+      if (solve_tc(h, ncols))
+        k_lus_update<0, PM_OZ8><<<g, 256, OZ_SMEM8, st>>>(items, k0);
+      else
+        k_lus_update<0><<<g, 256, 0, st>>>(items, k0);
+      ++h.nlaunch;
     }
   }
 }
@@ -594,7 +612,11 @@ static int sweeps(Handle& h, SolveBufs& B, double* b, int nrhs, int64_t ld) {
       if (!cnt) continue;
       k_fwd_prep<<<cnt, 256, 0, st>>>(v, sv[l], col, B.items); ++h.nlaunch;
       lus_apply(h, B.items, cnt, F.P, nrhs, 0, st);
-      k_fwd_upd<<<dim3(ncol * rt, ct, cnt), 256, 0, st>>>(v, sv[l], col, rt); ++h.nlaunch;
+      if (solve_tc(h, nrhs))
+        k_fwd_upd<PM_OZ8><<<dim3(ncol * rt, ct, cnt), 256, OZ_SMEM8, st>>>(v, sv[l], col, rt);
+      else
+        k_fwd_upd<PM_FMA><<<dim3(ncol * rt, ct, cnt), 256, 0, st>>>(v, sv[l], col, rt);
+      ++h.nlaunch;
     }
     if (l > 2) {
       FacLevel& Fp = h.fac[l - 1];
@@ -629,7 +651,11 @@ static int sweeps(Handle& h, SolveBufs& B, double* b, int nrhs, int64_t ld) {
       int cnt = colour_count(col, d, F.n);
       if (!cnt) continue;
       k_bwd_prep<<<cnt, 256, 0, st>>>(v, sv[l], col, y, B.items); ++h.nlaunch;
-      k_bwd_part<<<dim3(mt * ncol, ct, cnt), 256, 0, st>>>(v, sv[l], col, y, mt, B.part); ++h.nlaunch;
+      if (solve_tc(h, nrhs))
+        k_bwd_part<PM_OZ8><<<dim3(mt * ncol, ct, cnt), 256, OZ_SMEM8, st>>>(v, sv[l], col, y, mt, B.part);
+      else
+        k_bwd_part<PM_FMA><<<dim3(mt * ncol, ct, cnt), 256, 0, st>>>(v, sv[l], col, y, mt, B.part);
+      ++h.nlaunch;
       k_bwd_sum<<<dim3(mt, ct, cnt), 256, 0, st>>>(v, sv[l], col, y, B.part); ++h.nlaunch;
       lus_apply(h, B.items, cnt, F.P, nrhs, 1, st);
       k_bwd_out<<<cnt, 256, 0, st>>>(v, sv[l], col); ++h.nlaunch;
@@ -657,6 +683,14 @@ static int solve_attrs(Handle& h) {
                                            (int)(sizeof(double) * MAX_GATHER)));
     AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_small<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * LS_MAXN * 4)));
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<1, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           OZ_SMEM8));
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_lus_update<0, PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           OZ_SMEM8));
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_upd<PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           OZ_SMEM8));
+    AIFMM_CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_part<PM_OZ8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           OZ_SMEM8));
     done[dv] = true;
   }
   return HOK;
