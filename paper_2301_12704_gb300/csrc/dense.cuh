@@ -349,13 +349,19 @@ struct SolveItem {
   const int* perm;   // net row permutation of ipiv (solve sweeps only), or null
 };
 
-// column maxima of |A| (n x n), one block per item
+// column maxima of |A| (n x n), one block per item, one warp per column
+// (lanes over the rows, coalesced; fmax ignores NaNs and is order-free, so
+// the result is that of a sequential scan)
 static __global__ void k_colmax(const LuItem* items, double* out, int stride) {
   LuItem it = items[blockIdx.x];
-  for (int c = threadIdx.x; c < it.n; c += blockDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < it.n; c += nw) {
+    const double* col = it.a + (size_t)c * it.ld;
     double mx = 0.0;
-    for (int i = 0; i < it.n; ++i) mx = fmax(mx, fabs(it.a[i + (size_t)c * it.ld]));
-    out[(size_t)blockIdx.x * stride + c] = mx;
+    for (int i = lane; i < it.n; i += 32) mx = fmax(mx, fabs(col[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) out[(size_t)blockIdx.x * stride + c] = mx;
   }
 }
 
@@ -650,7 +656,37 @@ __device__ inline void ipiv_to_perm(const int* ipiv, int n, int* perm) {
   }
 }
 
-static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) { ipiv_to_perm(ipiv, n, perm); }
+// the same in shared memory (n <= 4096): the interchanges are read in one
+// coalesced pass, the sequential composition runs on shared memory in one
+// thread, and the permutation is written back in one pass; one CTA
+__device__ inline void ipiv_to_perm_sm(const int* ipiv, int n, int* perm, int* sp, int* sq) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sp[i] = i;
+    sq[i] = ipiv[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) {
+      const int q = sq[k];
+      if (q != k) {
+        const int x = sp[k];
+        sp[k] = sp[q];
+        sp[q] = x;
+      }
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sp[i];
+}
+
+// dynamic shared memory 2 n ints (n <= 4096); the global form beyond
+static __global__ void k_ipiv_perm(const int* ipiv, int n, int* perm) {
+  extern __shared__ int ipsm[];
+  if (n > 4096) {
+    if (threadIdx.x == 0) ipiv_to_perm(ipiv, n, perm);
+    return;
+  }
+  ipiv_to_perm_sm(ipiv, n, perm, ipsm, ipsm + n);
+}
 
 // trailing update after diagonal block k0: lower -> rows below, upper -> rows
 // above:  X[rows] -= A[rows, k0:k0+TB] X[k0:k0+TB];  grid (coltiles, rowtiles, items)

@@ -345,23 +345,40 @@ __device__ __noinline__ WsBlk ws_block(const LV v, int b, int s, int side, int c
 
 // the pending blocks of each box side and their column offsets in W after
 // the basis (stencil-slot order), the gathered column count and r_b; the
-// threshold accumulator cleared.  One thread per (box, side).
+// threshold accumulator cleared.  One warp per (box, side).
 __global__ void k_cmp_list(LV v, Cmp c, int nsides) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= c.cnt * nsides) return;
+  // one warp per (box, side), a lane per stencil slot, offsets by a warp
+  // prefix sum (in stencil-slot order, as a sequential walk would give)
+  const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (x >= c.cnt * nsides) return;   // the whole warp
   const int t = x / nsides, side = x % nsides;
   const int b = cbox(c, v, t);
   const int rb = v.r[b];
   int* off = c.boff + ((size_t)t * 2 + side) * v.ns5;
   int o = rb;
-  for (int sl = 0; sl < v.ns5; ++sl) {
-    WsBlk w = ws_block(v, b, sl, side, c.col);
-    off[sl] = w.ok ? o : -1;
-    if (w.ok) o += side == 0 ? w.cols : w.rows;
+  for (int s0 = 0; s0 < v.ns5; s0 += 32) {
+    const int sl = s0 + lane;
+    int w = 0;
+    bool ok = false;
+    if (sl < v.ns5) {
+      const WsBlk blk = ws_block(v, b, sl, side, c.col);
+      ok = blk.ok != 0;
+      w = ok ? (side == 0 ? blk.cols : blk.rows) : 0;
+    }
+    int incl = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (sl < v.ns5) off[sl] = ok ? o + incl - w : -1;
+    o += __shfl_sync(0xffffffffu, incl, 31);
   }
-  c.nc[t * 2 + side] = o;
-  if (side == 0) c.rold[t] = rb;
-  c.tau[t * 2 + side] = 0.0;
+  if (lane == 0) {
+    c.nc[t * 2 + side] = o;
+    if (side == 0) c.rold[t] = rb;
+    c.tau[t * 2 + side] = 0.0;
+  }
 }
 
 // gather [U_b | row fill-ins] (side 0) and [V_b | column fill-ins^T] (side 1)
@@ -1282,12 +1299,13 @@ __global__ void k_coupled(LV v, Elim e) {
   e.sv[t] = si;
 }
 
-// net row permutation of each box's pivot LU, for the solve sweeps; one thread per box
+// net row permutation of each box's pivot LU, for the solve sweeps; one CTA
+// per box, through shared memory (dynamic: 2 P ints)
 __global__ void k_piv_perm(LV v, int col, int cnt) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  int b = colour_box(col, t, v.d, v.l);
-  ipiv_to_perm(v.piv(b), v.m[b] + v.r[b], v.pp(b));
+  extern __shared__ int ppsm[];
+  const int t = blockIdx.x;
+  const int b = colour_box(col, t, v.d, v.l);
+  ipiv_to_perm_sm(v.piv(b), v.m[b] + v.r[b], v.pp(b), ppsm, ppsm + v.P);
 }
 
 // Piv = [[K_bb, U_b], [V_b^T, 0]] into the LU storage; grid cnt
@@ -2003,7 +2021,7 @@ static int factor_level(Handle& h, int l) {
     c.skip = ib + 6 * cnt;
     GroupTimer* gt = new GroupTimer(h, Handle::G_COMPRESS);
     dp.begin("gather");
-    k_cmp_list<<<(cnt * nsides + 127) / 128, 128, 0, st>>>(v, c, nsides); ++h.nlaunch;
+    k_cmp_list<<<(cnt * nsides * 32 + 127) / 128, 128, 0, st>>>(v, c, nsides); ++h.nlaunch;
     k_cmp_gather<<<dim3(cnt * nsides, F.ns5 + 1), 256, 0, st>>>(v, c, nsides); ++h.nlaunch;
     dp.end();
     k_cmp_skip<<<(cnt + 127) / 128, 128, 0, st>>>(v, c); ++h.nlaunch;
@@ -2150,7 +2168,7 @@ static int factor_level(Handle& h, int l) {
         dp.end();
       }
     }
-    k_piv_perm<<<(cnt + 127) / 128, 128, 0, st>>>(v, col, cnt); ++h.nlaunch;
+    k_piv_perm<<<cnt, 128, sizeof(int) * 2 * (size_t)F.P, st>>>(v, col, cnt); ++h.nlaunch;
     delete gt;
     // ---- Z = U^-1 (L^-1 P B) and the Schur update
     gt = new GroupTimer(h, Handle::G_ZSOLVE);
@@ -2372,7 +2390,8 @@ int run_factor(Handle& h) {
       k_lu_gemm<PM_FMA><<<dim3(tiles, tiles, 1), 256, 0, st>>>(it, k0);
     ++h.nlaunch;
   }
-  k_ipiv_perm<<<1, 1, 0, st>>>(h.top_ipiv, h.ntop, h.top_perm); ++h.nlaunch;
+  k_ipiv_perm<<<1, 128, h.ntop <= 4096 ? sizeof(int) * 2 * (size_t)h.ntop : 0, st>>>(h.top_ipiv, h.ntop, h.top_perm);
+  ++h.nlaunch;
   dpf.end();
   dpf.report(1);
   h.flops_factor += 2.0 / 3.0 * (double)h.ntop * h.ntop * h.ntop;
