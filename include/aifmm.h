@@ -249,6 +249,20 @@ int aifmm_levels(aifmm_h h);
  * aifmm_build); -1 if h is NULL. */
 int aifmm_device(aifmm_h h);
 
+/* Move the handle's later work to a new CUDA stream, created by the library
+ * with stream priority `priority` (lower numbers run first; CUDA clamps the
+ * value into the device's range, so a large negative value asks for the
+ * highest priority).  The handle's current stream is synchronised first, so
+ * the caller needs no ordering between the two; a stream the library had
+ * created is destroyed, a stream passed in aifmm_options.stream is left to
+ * its owner.  For a request loop: factorisations run on default-priority
+ * streams (the lowest) and solves against finished factorisations on
+ * high-priority ones, so that solve kernels are scheduled ahead of pending
+ * factorisation kernels of other handles.  The paper has no counterpart to
+ * this call.  INVALID if h is NULL, CUDA if the stream cannot be created (the
+ * handle keeps its stream). */
+aifmm_status aifmm_set_priority(aifmm_h h, int priority);
+
 /* Message of the last error on h (or of the last failed aifmm_build when h is
  * NULL).  Valid until the next call on the handle. */
 const char* aifmm_last_error(aifmm_h h);

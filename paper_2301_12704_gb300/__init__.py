@@ -68,6 +68,7 @@ def lib():
         L.aifmm_factor.argtypes = [vp]
         L.aifmm_solve.argtypes = [vp, vp, vp, cint, i64]
         L.aifmm_solve_noalloc.argtypes = [vp, vp, vp, cint, i64]
+        L.aifmm_set_priority.argtypes = [vp, cint]
         L.aifmm_noalloc_scratch_bytes.argtypes = []
         L.aifmm_noalloc_scratch_bytes.restype = i64
         L.aifmm_matvec.argtypes = [vp, vp, vp, cint, i64]
@@ -355,6 +356,12 @@ def aifmm_stats(h: Handle) -> dict:
         v = getattr(s, f)
         out[f] = list(v) if hasattr(v, "__len__") else v
     return out
+
+
+def aifmm_set_priority(h: Handle, priority: int) -> None:
+    """Move the handle's later work to a new library stream of this CUDA
+    priority (lower runs first; clamped to the device's range)."""
+    _check(lib().aifmm_set_priority(h.raw, int(priority)), h.raw)
 
 
 def aifmm_levels(h: Handle) -> int:

@@ -654,6 +654,25 @@ int aifmm_levels(aifmm_h c) { return c ? c->h.L : 0; }
 
 int aifmm_device(aifmm_h c) { return c ? c->h.device : -1; }
 
+aifmm_status aifmm_set_priority(aifmm_h c, int priority) {
+  if (!c) return AIFMM_ERR_INVALID;
+  Handle& h = c->h;
+  AIFMM_ON_DEVICE(h);
+  if (h.stream && cudaStreamSynchronize(h.stream) != cudaSuccess) {
+    h.err = std::string("aifmm_set_priority: ") + cudaGetErrorString(cudaGetLastError());
+    return AIFMM_ERR_CUDA;
+  }
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority) != cudaSuccess) {
+    h.err = std::string("cudaStreamCreateWithPriority: ") + cudaGetErrorString(cudaGetLastError());
+    return AIFMM_ERR_CUDA;
+  }
+  if (h.own_stream && h.stream) cudaStreamDestroy(h.stream);
+  h.stream = s;
+  h.own_stream = true;
+  return AIFMM_OK;
+}
+
 const char* aifmm_last_error(aifmm_h c) {
   if (!c) return g_build_err.c_str();
   return c->h.err.c_str();

@@ -16,7 +16,9 @@ aifmm_solve, and the columns are split back per request.  Factor requests
 run on a worker thread, each on its handle's own CUDA stream, so their
 kernels overlap on the device with the batched solves issued by the serving
 thread on other handles' streams; requests that arrive while others are on
-the GPU join the next batch or wait for memory.
+the GPU join the next batch or wait for memory.  Once factored, a handle
+moves to a high-priority stream (aifmm_set_priority), so the solve batches
+are scheduled ahead of the kernels of factorisations still running.
 
 Memory model: the factorisation's blocks are dense per box and stencil slot,
 sized by the level's largest box, so at a fixed depth they grow like
@@ -37,7 +39,12 @@ import time
 
 import numpy as np
 
-from . import aifmm_build, aifmm_destroy, aifmm_factor, aifmm_solve, aifmm_stats
+from . import aifmm_build, aifmm_destroy, aifmm_factor, aifmm_set_priority, aifmm_solve, aifmm_stats
+
+# CUDA stream priority of the solves against finished factorisations (CUDA
+# clamps it to the device's highest); factorisations keep the default, the
+# lowest, so pending solve kernels are scheduled ahead of theirs
+SOLVE_PRIORITY = -1000
 
 # conservative bytes per (point x leaf occupancy) before a factorisation of
 # that dimension has been measured
@@ -149,6 +156,7 @@ class Server:
             try:
                 h = aifmm_build(r.points, r.kernel, r.diag, r.tol, r.leaf, length=r.length)
                 aifmm_factor(h)
+                aifmm_set_priority(h, SOLVE_PRIORITY)
                 nbytes = float(aifmm_stats(h)["bytes_resident"])
                 st = "done"
             except Exception as e:      # reported on the request, the loop goes on

@@ -68,3 +68,9 @@ def test_nugget_and_eta_arguments_checked_before_gpu_work():
     k = A.Kernel(A.GAUSS, 2, float("inf"), 0.1, 0.0)
     st = lib.aifmm_build(C.c_void_p(pts.ctypes.data), 64, C.byref(k), 1e-8, 16, None, C.byref(out))
     assert st == 1
+
+
+def test_set_priority_on_a_null_handle_is_refused():
+    """aifmm_set_priority validates its handle before any CUDA call."""
+    lib = A.lib()
+    assert lib.aifmm_set_priority(None, -5) == 1

@@ -5,7 +5,10 @@
   same solution, bit for bit, as the diagonal 1.01 given explicitly.
 * Any admissibility parameter eta >= sqrt(dim) classifies the boxes of a
   uniform tree as the default does (Sec. 2.2): the same solution, bit for
-  bit."""
+  bit.
+* A handle moved to a high-priority stream after its factorisation
+  (aifmm_set_priority, for request loops) solves as before, bit for bit,
+  twice in a row."""
 import numpy as np
 import pytest
 
@@ -48,3 +51,17 @@ def test_eta_at_or_above_sqrt_dim_gives_the_same_lists(A):
     x0 = _solve(A, w, pts, b)
     for eta in (np.sqrt(2.0), 3.0):
         assert np.array_equal(x0, _solve(A, w, pts, b, eta=eta))
+
+
+def test_solves_after_a_priority_change_are_unchanged(A):
+    w = W.log2d(3000, seed=15, leaf=32)
+    pts, b = W.points_and_rhs(w, nrhs=2)
+    h = A.aifmm_build(pts, w.kernel, w.diag, w.tol, w.leaf)
+    A.aifmm_factor(h)
+    x0 = A.aifmm_solve(h, b)
+    A.aifmm_set_priority(h, -1000)       # clamped to the device's highest
+    x1 = A.aifmm_solve(h, b)
+    A.aifmm_set_priority(h, 0)
+    x2 = A.aifmm_solve(h, b)
+    A.aifmm_destroy(h)
+    assert np.array_equal(x0, x1) and np.array_equal(x0, x2)

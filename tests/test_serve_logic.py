@@ -19,6 +19,7 @@ class FakeHandle:
         self.alive = True
         self.n = len(pts)
         self.solves = 0
+        self.raised = False
 
 
 @pytest.fixture
@@ -35,6 +36,7 @@ def fake(monkeypatch):
 
     def solve(h, B):
         assert h.alive, "solve on an evicted factorisation"
+        assert h.raised, "solve before the factorisation moved to the solve priority"
         h.solves += 1
         return np.linalg.solve(h.A, B)
 
@@ -51,6 +53,13 @@ def fake(monkeypatch):
     monkeypatch.setattr(S, "aifmm_solve", solve)
     monkeypatch.setattr(S, "aifmm_stats", stats)
     monkeypatch.setattr(S, "aifmm_destroy", destroy)
+
+    def set_priority(h, p):
+        assert h.alive and p == S.SOLVE_PRIORITY
+        h.raised = True
+        state["raised"] = state.get("raised", 0) + 1
+
+    monkeypatch.setattr(S, "aifmm_set_priority", set_priority)
     return state
 
 
@@ -77,6 +86,8 @@ def test_batched_solves_are_the_requests_own(fake):
     # with 400 requests/s several solves wait on one factorisation: batches form
     assert max(r.batch - r.rhs.shape[1] for r in reqs if r.kind == "solve") > 0
     assert m["mean_batch_cols"] > np.mean([r.rhs.shape[1] for r in reqs if r.kind == "solve"])
+    # every factorisation moved to the solve priority once factored
+    assert fake["raised"] == len(facs)
 
 
 def test_admission_evicts_idle_factorisations(fake):
