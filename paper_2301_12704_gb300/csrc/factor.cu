@@ -1069,12 +1069,8 @@ __global__ void __launch_bounds__(256) k_cmp_col_mirror(LV v, Cmp c) {
     bool both = db == b;
     if (!both && colour_of(q, v.d) == c.col) both = !c.skip[colour_index(q, v.d, v.n)];
     if (!both) {
-      // A_db := (A_bd)^T, r_db x rn
-      const double* src = v.ly(b, x);
-      for (int e = threadIdx.x; e < nrows * rn; e += blockDim.x) {
-        const int i = e % nrows, j = e / nrows;
-        blk[i + (size_t)j * v.R] = src[j + (size_t)i * v.R];
-      }
+      // A_db := (A_bd)^T, r_db x rn (the branch is the same for the whole CTA)
+      copy_transposed(v.ly(b, x), v.R, blk, v.R, nrows, rn);
       return;
     }
     // blk[0..nrows, 0..rn) := blk[.., 0..ro) R_b^T, TR_CG rows at a time
@@ -1122,12 +1118,7 @@ __global__ void __launch_bounds__(256) k_cmp_col_mirror(LV v, Cmp c) {
   if (colour_of(q, v.d) < c.col) return;   // eliminated partner: part of the A_qb mirror
   const int qb = morton_key(q, v.d, v.l);
   const int mq = sw.rows;
-  double* dst = v.xy(qb, slot5(q, bc, v.d));
-  const double* src = v.lx(b, s5);
-  for (int e = threadIdx.x; e < mq * rn; e += blockDim.x) {
-    const int i = e % mq, j = e / mq;
-    dst[i + (size_t)j * v.M] = src[j + (size_t)i * v.R];
-  }
+  copy_transposed(v.lx(b, s5), v.R, v.xy(qb, slot5(q, bc, v.d)), v.M, mq, rn);
 }
 
 // column side fill-ins: P2L_qb -> A_qb += P2L_qb V~ ; P2P_qb -> M2P_qb = P2P_qb V~
