@@ -34,8 +34,8 @@ static long fail_at() {
 // allocations and frees never synchronise the device, so handles driven from
 // several host threads (many problems, the serving loop) do not stall each
 // other, and a new handle reuses the blocks of destroyed ones instead of
-// asking the driver again.  The pool's memory returns to the driver at
-// process exit.
+// asking the CUDA driver again.  The pool's memory returns to the CUDA
+// driver at process exit.
 static cudaMemPool_t lib_pool(int dev) {
   static cudaMemPool_t pools[64] = {};
   static std::mutex mu;
