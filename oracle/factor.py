@@ -198,8 +198,8 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool 
     (reading R2): row side into U_b, column side into V_b.  ``symmetric``
     (reading R13, for A = A^T with V = U): the RRQR of the row side gives
     both new bases, V~_b = U~_b.  ``log`` (optional dict) receives, under
-    (l, b), the row side's RRQR record: old rank, |R_kk| sequence, threshold
-    and new rank (recording only)."""
+    (l, b), the row side's RRQR record: old rank, |R_kk| sequence, threshold,
+    new rank and the basis U_b it started from (recording only)."""
     _ensure_aux(S, l, b)
     Yb, Lb, yb, zb = ("Y", l, b), ("L", l, b), ("y", l, b), ("z", l, b)
     rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
@@ -229,7 +229,7 @@ def compress_box(S: BlockSystem, T, l: int, b: int, eps: float, symmetric: bool 
     rn = max(rU, rV)
     if log is not None:
         log[(l, b)] = {"r_old": r, "rdiag": np.array(dU), "tau": tauU, "rank": rn, "m": m,
-                       "ncols": Frow.shape[1], "partners": list(wcols)}
+                       "ncols": Frow.shape[1], "partners": list(wcols), "U": U.copy()}
     assert rn <= m
     if rn == 0:
         # every fill-in column is exactly zero: drop them
@@ -546,7 +546,7 @@ def eliminate(S: BlockSystem, PR, PC, box=None) -> Step:
 
 
 def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = True, grouping: str = "box",
-           symmetric: bool = False):
+           symmetric: bool = False, bases: dict | None = None):
     """Algorithm 2 on the extended system of (tree, kernel, nn).
 
     order    -- 'paper' or 'colour' (reading R1)
@@ -557,12 +557,20 @@ def factor(tree, kernel, nn, eps: float, order: str = "paper", compress: bool = 
                 printed, Sec. 3.2.1-3.2.3)
     symmetric -- per-box grouping with one RRQR per box for both bases
                 (reading R13; the kernel must be symmetric)
+    bases    -- optional dict, filled with every box's basis U_b (its X_b x
+                z_b block) as its level starts, keyed (l, b); None where the
+                box has no basis yet (recording only)
     """
     T = tree
     S = assemble(T, kernel, nn)
     F = Factorization(T, nn, eps, order, compress)
     F.sizes_r, F.sizes_c = S.rsize, S.csize
     for l in range(T.L, 1, -1):
+        if bases is not None:
+            for b in T.order(l, order):
+                zb = ("z", l, b)
+                rs = [k for k in rowset(T, l, b) if S.rsize.get(k, 0)]
+                bases[(l, b)] = S.dense(rs, [zb]) if S.csize.get(zb, 0) and rs else None
         for b in T.order(l, order):
             if compress and grouping == "pair":
                 F.ncompress += compress_pairs(S, T, l, b, eps)
